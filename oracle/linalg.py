@@ -1,0 +1,148 @@
+"""Householder QR with a fixed completion rule, and the Lanczos matrix exponential
+(oracle; test infrastructure only).
+
+The paper re-gauges the tree between local updates with a matrix factorisation
+("the SVD is a central element in the numerical algorithm for updating and
+normalising the TTNS", Results, energy-surface section) and evolves every tensor
+with its local effective Hamiltonian (Results, "TDVP for TTNS").  The
+Supplement that fixes the algorithm is not part of the paper, so the readings
+below are used (they are the same on the CUDA side):
+
+QR  (complex Householder, column by column)
+    For column j the remaining sub-column x = M[j:, j] is reflected onto
+    alpha e_0 with alpha = -exp(i arg x_0) ||x||.  If ||x|| <= 1e-8 ||M||_F the
+    reflector is the identity and R_jj = 0.  Q = H_0 ... H_{n-1} I[:, :n].
+    Finally every column j is re-phased so that R_jj is real and >= 0.
+    The threshold sits four orders above the Krylov tolerance: a column that
+    is zero in exact arithmetic but carries Krylov truncation error (~1e-12)
+    must not pick the completion direction, or two correct implementations
+    (different rounding, different Krylov lengths) follow different one-site
+    TDVP trajectories.
+
+Krylov exponential  y = exp(-i s H) v  (s = time / hbar, any sign)
+    Lanczos with classical Gram-Schmidt run twice against all previous vectors
+    (full re-orthogonalisation).  After step j the tridiagonal T is
+    exponentiated through its eigen-decomposition; the step stops when
+    beta_{j+1} |e_j^T exp(-i s T) e_0| <= tol (Saad's estimate) or j + 1 == mmax.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+QR_NULL_REL = 1e-8
+KRYLOV_TOL = 1e-12
+KRYLOV_MMAX = 30
+
+
+def householder_qr(M: np.ndarray):
+    """QR of an m x n complex matrix (m >= n) with the completion rule above.
+
+    Returns Q (m x n, orthonormal columns) and R (n x n, upper triangular with a
+    real non-negative diagonal) such that M = Q R.
+    """
+    M = np.array(M, dtype=complex)
+    m, n = M.shape
+    if m < n:
+        raise ValueError("householder_qr needs rows >= cols")
+    fro = np.sqrt(np.sum(np.abs(M) ** 2))
+    thr = QR_NULL_REL * fro
+    W = M.copy()
+    vs = []
+    for j in range(n):
+        x = W[j:, j]
+        sigma = np.sqrt(np.sum(np.abs(x) ** 2))
+        if sigma <= thr or sigma == 0.0:
+            vs.append(None)
+            # the identity reflector leaves column j as it is below the diagonal;
+            # only its diagonal entry is kept in R, set to zero
+            W[j, j] = 0.0
+            W[j + 1:, j] = 0.0
+            continue
+        x0 = x[0]
+        phase = x0 / abs(x0) if abs(x0) > 0.0 else 1.0 + 0.0j
+        alpha = -phase * sigma
+        v = x.copy()
+        v[0] -= alpha
+        vnorm2 = np.real(np.vdot(v, v))
+        # apply H = I - 2 v v^H / (v^H v) to the trailing block
+        sub = W[j:, j:]
+        coef = (2.0 / vnorm2) * (v.conj() @ sub)
+        sub -= np.outer(v, coef)
+        W[j:, j:] = sub
+        W[j, j] = alpha
+        W[j + 1:, j] = 0.0
+        vs.append(v)
+    R = np.triu(W[:n, :n])
+    # Q = H_0 H_1 ... H_{n-1} applied to the first n columns of the identity
+    Q = np.zeros((m, n), dtype=complex)
+    Q[np.arange(n), np.arange(n)] = 1.0
+    for j in range(n - 1, -1, -1):
+        v = vs[j]
+        if v is None:
+            continue
+        vnorm2 = np.real(np.vdot(v, v))
+        sub = Q[j:, :]
+        coef = (2.0 / vnorm2) * (v.conj() @ sub)
+        Q[j:, :] = sub - np.outer(v, coef)
+    # make the diagonal of R real and non-negative
+    for j in range(n):
+        r = R[j, j]
+        if abs(r) > 0.0:
+            ph = r / abs(r)
+            Q[:, j] *= ph
+            R[j, :] *= np.conj(ph)
+            R[j, j] = abs(r)
+    return Q, R
+
+
+def expm_tridiag_e0(alpha: np.ndarray, beta: np.ndarray, s: float) -> np.ndarray:
+    """exp(-i s T) e_0 for the real symmetric tridiagonal T (diagonal alpha,
+    off-diagonal beta), through T = S diag(w) S^T."""
+    m = alpha.size
+    T = np.diag(alpha)
+    if m > 1:
+        T += np.diag(beta[: m - 1], 1) + np.diag(beta[: m - 1], -1)
+    w, S = np.linalg.eigh(T)
+    return S @ (np.exp(-1j * s * w) * S[0, :])
+
+
+def expm_lanczos(apply_H, v: np.ndarray, s: float, tol: float = KRYLOV_TOL,
+                 mmax: int = KRYLOV_MMAX, stats: dict | None = None) -> np.ndarray:
+    """y = exp(-i s H) v for Hermitian H given as a matrix-free apply_H(x)."""
+    shape = v.shape
+    v = np.asarray(v, dtype=complex).reshape(-1)
+    beta0 = np.linalg.norm(v)
+    if beta0 == 0.0:
+        return v.reshape(shape).copy()
+    n = v.size
+    mmax = min(mmax, n)
+    Qk = np.zeros((mmax, n), dtype=complex)
+    alpha = np.zeros(mmax)
+    beta = np.zeros(mmax)
+    Qk[0] = v / beta0
+    u = None
+    m = 0
+    for j in range(mmax):
+        w = np.asarray(apply_H(Qk[j].reshape(shape)), dtype=complex).reshape(-1)
+        alpha[j] = np.real(np.vdot(Qk[j], w))
+        w = w - alpha[j] * Qk[j]
+        if j > 0:
+            w = w - beta[j - 1] * Qk[j - 1]
+        for _ in range(2):
+            w = w - Qk[: j + 1].T @ (Qk[: j + 1].conj() @ w)
+        b = np.linalg.norm(w)
+        beta[j] = b
+        u = expm_tridiag_e0(alpha[: j + 1], beta[:j], s)
+        m = j + 1
+        err = b * abs(u[j])
+        if err <= tol or j + 1 == mmax:
+            if err > tol and j + 1 < n:
+                if stats is not None:
+                    stats["not_converged"] = stats.get("not_converged", 0) + 1
+            break
+        Qk[j + 1] = w / b
+    if stats is not None:
+        stats["krylov_iters"] = stats.get("krylov_iters", 0) + m
+        stats["applies"] = stats.get("applies", 0) + m
+    y = beta0 * (u @ Qk[:m])
+    return y.reshape(shape)

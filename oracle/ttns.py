@@ -1,0 +1,348 @@
+"""One-site TDVP for a tree tensor network state (oracle; test infrastructure only).
+
+The paper evolves its TTNS with the time-dependent variational principle: every
+tensor is evolved in turn with a local effective Hamiltonian H_eff(t) built from
+the full many-body state at that moment (Results, "TTNS for vibronic quantum
+dynamics", last paragraph; Methods, "Tensor Network States").  The algorithm
+itself sits in the paper's Supplement, which is not part of the paper text; the
+reading used here is the one-site projector-splitting integrator on a tree:
+
+  S(tau) = visit(root) with
+    visit(v):  A_v <- exp(-i tau H_eff(v)) A_v
+               for each child c, in order:
+                   QR of A_v toward c (A_v <- Q, bond matrix C <- R); env(v -> c)
+                   C <- exp(+i tau H_bond(v, c)) C;  A_c <- C A_c (on A_c's parent leg)
+                   visit(c)
+                   QR of A_c toward v; env(c -> v); A_v <- R A_v (no evolution)
+  S*(tau) = the same operations in reverse order:
+    visit*(v): for each child c, in reverse order:
+                   QR of A_v toward c; env(v -> c); A_c <- R A_c (no evolution)
+                   visit*(c)
+                   QR of A_c toward v; env(c -> v)
+                   C <- exp(+i tau H_bond(c, v)) C;  A_v <- C A_v
+               A_v <- exp(-i tau H_eff(v)) A_v
+  one step of length dt = S(dt/2) followed by S*(dt/2).
+
+Environment blocks.  For a directed edge (u -> v), env(u -> v) describes the part
+of the tree on u's side of the edge, projected on the bond basis given by u's
+tensor when u is an isometry toward v:
+  'H'  the sum of all terms that lie entirely on u's side,
+  t    for every two-node term t with one end on each side, the projected
+       factor of its end on u's side.
+H_eff(v) is the sum of v's on-site term, every neighbour's 'H' block on the leg
+toward it, and every two-node term whose two ends lie in different slots of v
+(its physical leg, or the subtrees behind two different legs).
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+
+from .linalg import expm_lanczos, householder_qr, KRYLOV_TOL, KRYLOV_MMAX
+from .model import Tree, build_tree, initial_tensors, lowering
+
+HBAR = 0.6582119569  # eV fs
+
+
+def apply_factor(A: np.ndarray, leg: int, M: np.ndarray) -> np.ndarray:
+    """y[..., i, ...] = sum_k M[i, k] A[..., k, ...] on the given leg."""
+    return np.moveaxis(np.tensordot(M, A, axes=([1], [leg])), 0, leg)
+
+
+class TTNS:
+    def __init__(self, problem, tol: float = KRYLOV_TOL, mmax: int = KRYLOV_MMAX):
+        self.problem = problem
+        self.tree: Tree = build_tree(problem)
+        self.A: List[np.ndarray] = initial_tensors(self.tree)
+        self.tol = tol
+        self.mmax = mmax
+        self.stats: Dict[str, int] = {}
+        self.t = 0.0
+        t = self.tree
+        n = t.n
+        # subtree membership
+        self.sub = [set() for _ in range(n)]
+        for v in reversed(range(n)):
+            self.sub[v].add(v)
+            for c in t.children[v]:
+                self.sub[v] |= self.sub[c]
+        self.env: Dict[Tuple[int, int], Dict] = {}
+        self._init_envs()
+
+    # ------------------------------------------------------------------ tree helpers
+    def piece(self, u: int, v: int) -> set:
+        """Nodes on u's side of the edge (u, v)."""
+        t = self.tree
+        if t.parent[u] == v:
+            return self.sub[u]
+        return set(range(t.n)) - self.sub[v]
+
+    def toward(self, v: int, x: int) -> int:
+        """The neighbour of v on the path to node x (x != v)."""
+        t = self.tree
+        for c in t.children[v]:
+            if x in self.sub[c]:
+                return c
+        return t.parent[v]
+
+    def end_factor(self, u: int, e: int, op: np.ndarray, t_idx: int):
+        """(leg, matrix) of a term's end e seen from node u."""
+        tr = self.tree
+        if e == u:
+            return tr.phys_leg(u), op
+        w = self.toward(u, e)
+        return tr.leg_of(u, w), self.env[(w, u)][t_idx]
+
+    def crossing(self, u: int, v: int) -> List[Tuple[int, int]]:
+        """Terms crossing edge (u, v): list of (term index, end node on u's side)."""
+        P = self.piece(u, v)
+        out = []
+        for ti, c in enumerate(self.tree.couplings):
+            ina, inb = c.va in P, c.vb in P
+            if ina != inb:
+                out.append((ti, c.va if ina else c.vb))
+        return out
+
+    def node_terms(self, v: int, exclude: Optional[int] = None):
+        """Terms of H restricted to the slots of v (all neighbours but `exclude`).
+
+        Returns a list of terms, each a list of (leg, matrix) factors."""
+        tr = self.tree
+        terms = []
+        if tr.onsite[v] is not None:
+            terms.append([(tr.phys_leg(v), tr.onsite[v])])
+        for w in tr.neighbours(v):
+            if w == exclude:
+                continue
+            terms.append([(tr.leg_of(v, w), self.env[(w, v)]["H"])])
+        P = self.piece(v, exclude) if exclude is not None else set(range(tr.n))
+        for ti, c in enumerate(tr.couplings):
+            if c.va not in P or c.vb not in P:
+                continue
+            sa = "p" if c.va == v else self.toward(v, c.va)
+            sb = "p" if c.vb == v else self.toward(v, c.vb)
+            if sa == sb:
+                continue
+            fa = self.end_factor(v, c.va, c.opa, ti)
+            fb = self.end_factor(v, c.vb, c.opb, ti)
+            terms.append([fa, fb])
+        return terms
+
+    @staticmethod
+    def apply_terms(A: np.ndarray, terms) -> np.ndarray:
+        y = np.zeros_like(A)
+        for term in terms:
+            x = A
+            for leg, M in term:
+                x = apply_factor(x, leg, M)
+            y += x
+        return y
+
+    # ------------------------------------------------------------------ environments
+    def update_env(self, u: int, v: int) -> None:
+        """env(u -> v) from A_u, which must be an isometry toward v."""
+        tr = self.tree
+        Q = self.A[u]
+        lv = tr.leg_of(u, v)
+        others = [k for k in range(Q.ndim) if k != lv]
+        Qc = Q.conj()
+
+        def project(X):
+            return np.tensordot(Qc, X, axes=(others, others))
+
+        blocks = {"H": project(self.apply_terms(Q, self.node_terms(u, exclude=v)))}
+        for ti, e in self.crossing(u, v):
+            c = tr.couplings[ti]
+            op = c.opa if e == c.va else c.opb
+            leg, M = self.end_factor(u, e, op, ti)
+            blocks[ti] = project(apply_factor(Q, leg, M))
+        self.env[(u, v)] = blocks
+
+    def _init_envs(self) -> None:
+        tr = self.tree
+        order = []
+
+        def post(v):
+            for c in tr.children[v]:
+                post(c)
+            order.append(v)
+
+        post(0)
+        for v in order:
+            if tr.parent[v] >= 0:
+                self.update_env(v, tr.parent[v])
+
+    # ------------------------------------------------------------------ local maps
+    def heff(self, v: int, x: np.ndarray) -> np.ndarray:
+        return self.apply_terms(x, self.node_terms(v))
+
+    def hbond(self, u: int, w: int, X: np.ndarray) -> np.ndarray:
+        """H_bond(u, w) X for the bond matrix X[i_u, i_w]."""
+        Eu = self.env[(u, w)]
+        Ew = self.env[(w, u)]
+        y = Eu["H"] @ X + X @ Ew["H"].T
+        for ti, _ in self.crossing(u, w):
+            y = y + Eu[ti] @ X @ Ew[ti].T
+        return y
+
+    def qr_toward(self, v: int, u: int) -> np.ndarray:
+        """A_v <- Q (isometry toward u); returns R with R[i_v, i_u-old]."""
+        tr = self.tree
+        A = self.A[v]
+        l = tr.leg_of(v, u)
+        Am = np.moveaxis(A, l, -1)
+        shp = Am.shape
+        Q, R = householder_qr(Am.reshape(-1, shp[-1]))
+        self.A[v] = np.moveaxis(Q.reshape(shp), -1, l)
+        return R
+
+    def absorb(self, R: np.ndarray, u: int, v: int) -> None:
+        """A_u <- R on u's leg toward v."""
+        self.A[u] = apply_factor(self.A[u], self.tree.leg_of(u, v), R)
+
+    def forward(self, v: int, tau: float) -> None:
+        self.A[v] = expm_lanczos(lambda x: self.heff(v, x), self.A[v], tau / HBAR,
+                                 self.tol, self.mmax, self.stats)
+        self.stats["forward"] = self.stats.get("forward", 0) + 1
+
+    def backward(self, u: int, w: int, R: np.ndarray, tau: float) -> np.ndarray:
+        self.stats["backward"] = self.stats.get("backward", 0) + 1
+        return expm_lanczos(lambda X: self.hbond(u, w, X), R, -tau / HBAR,
+                            self.tol, self.mmax, self.stats)
+
+    # ------------------------------------------------------------------ sweeps
+    def _visit(self, v: int, tau: float) -> None:
+        tr = self.tree
+        self.forward(v, tau)
+        for c in tr.children[v]:
+            R = self.qr_toward(v, c)
+            self.update_env(v, c)
+            R = self.backward(v, c, R, tau)
+            self.absorb(R, c, v)
+            self._visit(c, tau)
+            R = self.qr_toward(c, v)
+            self.update_env(c, v)
+            self.absorb(R, v, c)
+
+    def _visit_adj(self, v: int, tau: float) -> None:
+        tr = self.tree
+        for c in reversed(tr.children[v]):
+            R = self.qr_toward(v, c)
+            self.update_env(v, c)
+            self.absorb(R, c, v)
+            self._visit_adj(c, tau)
+            R = self.qr_toward(c, v)
+            self.update_env(c, v)
+            R = self.backward(c, v, R, tau)
+            self.absorb(R, v, c)
+        self.forward(v, tau)
+
+    def step(self, dt: float) -> None:
+        self._visit(0, 0.5 * dt)
+        self._visit_adj(0, 0.5 * dt)
+        self.t += dt
+
+    # ------------------------------------------------------------------ observables
+    def norm(self) -> float:
+        return float(np.sqrt(np.sum(np.abs(self.A[0]) ** 2)))
+
+    def energy(self) -> float:
+        A = self.A[0]
+        return float(np.real(np.vdot(A, self.heff(0, A))) / np.real(np.vdot(A, A)))
+
+    def rho_el(self) -> np.ndarray:
+        """Reduced density matrix of the electronic node (the centre is at the root)."""
+        A = self.A[0]
+        pl = self.tree.phys_leg(0)
+        others = [k for k in range(A.ndim) if k != pl]
+        return np.tensordot(A, A.conj(), axes=(others, others))
+
+    def site_densities(self) -> Dict[int, np.ndarray]:
+        """Local reduced density matrices of every node with a physical leg,
+        by the downward pass of bond density matrices from the root."""
+        tr = self.tree
+        out = {0: self.rho_el()}
+        stack = []
+        A = self.A[0]
+        for c in tr.children[0]:
+            l = tr.leg_of(0, c)
+            others = [k for k in range(A.ndim) if k != l]
+            stack.append((c, np.tensordot(A, A.conj(), axes=(others, others))))
+        while stack:
+            v, rho_in = stack.pop()
+            Q = self.A[v]
+            # X[a, ...] = sum_a' rho_in[a', a] Q[a', ...]; contracting X with conj(Q)
+            # over a gives sum rho_in[a', a] Q[a', ...] conj(Q[a, ...])
+            X = apply_factor(Q, 0, rho_in.T)
+            if tr.phys[v] > 0:
+                pl = tr.phys_leg(v)
+                others = [k for k in range(Q.ndim) if k != pl]
+                out[v] = np.tensordot(X, Q.conj(), axes=(others, others))
+            for c in tr.children[v]:
+                l = tr.leg_of(v, c)
+                others = [k for k in range(Q.ndim) if k != l]
+                stack.append((c, np.tensordot(X, Q.conj(), axes=(others, others))))
+        return out
+
+    def occupations(self) -> np.ndarray:
+        """<a^+ a> of every chain site, chains in order, sites in chain order."""
+        tr = self.tree
+        dens = self.site_densities()
+        occ = []
+        for nodes in tr.chain_nodes:
+            for v in nodes:
+                d = tr.phys[v]
+                occ.append(float(np.real(np.sum(np.arange(d) * np.diag(dens[v])))))
+        return np.array(occ)
+
+    def populations(self) -> np.ndarray:
+        return np.real(np.diag(self.rho_el())).copy()
+
+    # ------------------------------------------------------------------ dense state
+    def to_dense(self) -> np.ndarray:
+        """The full state vector; basis order: electronic index, then the chain
+        sites in node order (only for tiny trees)."""
+        tr = self.tree
+
+        def contract(v):
+            # returns tensor with legs [parent bond?] + [phys of subtree nodes in node order]
+            T = self.A[v]
+            legs_nodes = []  # node id owning each physical leg currently in T (after bonds)
+            # children bond legs sit at positions (1 if parent) .. ; contract them one by one
+            off = 1 if tr.parent[v] >= 0 else 0
+            nchild = len(tr.children[v])
+            # move own phys leg to the end first
+            cur = T
+            phys_owner = []
+            if tr.phys[v] > 0:
+                phys_owner = [v]
+            for k, c in enumerate(tr.children[v]):
+                S, owners = contract(c)
+                # the child's bond leg is at position off (we consume children in order)
+                cur = np.tensordot(cur, S, axes=([off], [0]))
+                # now legs: [parent?] + remaining children + own phys(es) + child's phys legs
+                phys_owner = phys_owner + owners
+            return cur, phys_owner
+
+        T, owners = contract(0)
+        # T legs: own phys of root then all others in the order they were appended
+        order = np.argsort(owners, kind="stable")
+        T = np.transpose(T, order)
+        return T.reshape(-1)
+
+
+def run(problem, n_steps: Optional[int] = None, record_every: int = 1, occupations: bool = True):
+    """Runs the sweep and returns the populations (and chain occupations) after
+    every `record_every` steps, starting with t = 0."""
+    st = TTNS(problem)
+    n = problem.n_steps if n_steps is None else n_steps
+    pops = [st.populations()]
+    occs = [st.occupations()] if occupations else []
+    for k in range(n):
+        st.step(problem.dt)
+        if (k + 1) % record_every == 0:
+            pops.append(st.populations())
+            if occupations:
+                occs.append(st.occupations())
+    return st, np.array(pops), (np.array(occs) if occupations else None)
