@@ -1,0 +1,194 @@
+/*
+ * ttns.h - C ABI of the GB300 tree-tensor-network-state (TTNS) sweep library.
+ *
+ * The library runs the real-time sweep of arXiv:1710.01362 ("Multi-dimensional
+ * Tensor Network Simulation of Open Quantum Dynamics in Singlet Fission") on
+ * one GPU.  The paper's problem statement is the star Hamiltonian (Eq. 2):
+ *
+ *     H = H_S + sum_i [ Wbar_i ||lambda_i|| (a_i0 + a_i0^+)/sqrt(2) + H_c,i ],
+ *     H_c,i = sum_n omega_in a_in^+ a_in + sum_n t_in (a_in^+ a_i,n+1 + h.c.),
+ *
+ * a tree tensor network state with the electronic system at the root and one
+ * bosonic chain per environment (Results, "TTNS for vibronic quantum dynamics";
+ * Methods, "Tensor Network States"), optionally with a balanced binary tree of
+ * entanglement-renormalisation nodes between the root and the chains, evolved
+ * with the time-dependent variational principle (one tensor at a time with its
+ * local effective Hamiltonian), starting from the zero-temperature vacuum with
+ * one electronic state populated.
+ *
+ * Conventions (all calls):
+ *   - energies in eV, times in fs, hbar = 0.6582119569 eV fs;
+ *   - complex arrays are interleaved (re, im) doubles, matrices row-major;
+ *   - every input array is copied during the call; the caller keeps ownership;
+ *   - output arrays are caller-owned host buffers of the stated size;
+ *   - no exception crosses the ABI: every call returns a ttns_status, and
+ *     ttns_last_error() gives a one-line reason for the last failure;
+ *   - work is ordered on the CUDA stream given in ttns_options (NULL = legacy
+ *     default stream); calls that return host data synchronise that stream.
+ *   - arguments are validated before anything is allocated: bad sizes, NULL
+ *     pointers and non-Hermitian H_S / Wbar (tolerance 1e-12) give TTNS_E_INVALID.
+ */
+#ifndef TTNS_H
+#define TTNS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ttns_tree ttns_tree; /* opaque, library-owned */
+
+typedef enum {
+  TTNS_OK = 0,
+  TTNS_E_INVALID = 1,       /* bad argument */
+  TTNS_E_OOM = 2,           /* device allocation failed */
+  TTNS_E_CUDA = 3,          /* a CUDA call failed */
+  TTNS_E_NOT_CONVERGED = 4, /* a Krylov exponential hit krylov_mmax above tolerance */
+  TTNS_E_TIMEOUT = 5,       /* a device-side wait gave up (bounded spin) */
+  TTNS_E_NONFINITE = 6,     /* a norm became NaN or Inf */
+  TTNS_E_IO = 7             /* checkpoint file error */
+} ttns_status;
+
+typedef enum {
+  TTNS_FP64 = 0,  /* every contraction in FP64 */
+  TTNS_MIXED = 1  /* contractions in FP32-class arithmetic with FP64 Lanczos, QR, gauge moves */
+} ttns_precision;
+
+typedef struct {
+  int precision;         /* ttns_precision */
+  double krylov_tol;     /* Krylov stopping tolerance, 0 -> 1e-12 */
+  int krylov_mmax;       /* maximum Krylov dimension, 0 -> 30 (at most 32) */
+  void* cuda_stream;     /* cudaStream_t used by every call, NULL = default stream */
+  int er_tree;           /* 1: balanced binary ER tree between the root and the chains */
+  int D_er;              /* requested bond dimension between ER nodes (er_tree only) */
+  int init_state;        /* electronic state populated at t = 0 (when psi_el is NULL) */
+  const double* psi_el;  /* optional initial electronic amplitudes, n_el complex (copied) */
+  int record;            /* 1: keep rho_S after every step in a device trajectory buffer */
+  int max_record;        /* capacity of that buffer in steps (0 -> 4096) */
+  int cluster_ctas;      /* CTAs per cluster team (0 -> 16) */
+  int grid_ctas;         /* CTAs of the persistent grid (0 -> one per SM) */
+} ttns_options;
+
+/* One tree's Hamiltonian (Eq. 2) and truncation.
+ *   n_el            number of electronic (diabatic) states, >= 1
+ *   H_S             n_el*n_el complex, Hermitian (shifted internally by -tr(H_S)/n_el)
+ *   n_env           number of environments (chains), >= 1 (a power of two >= 2 with er_tree)
+ *   W_bar           n_env*n_el*n_el complex, each Hermitian: coupling pattern Wbar_i
+ *   rc_coupling     n_env: ||lambda_i|| in eV (reaction-coordinate coupling)
+ *   chain_len       n_env: L_i >= 1 sites
+ *   chain_omega     n_env pointers to L_i onsite energies omega_in (eV)
+ *   chain_hop       n_env pointers to L_i - 1 hoppings t_in (eV) (may be NULL when L_i == 1)
+ *   local_dim       n_env: Fock truncation d_i >= 2 of every site of chain i
+ *   bond_dim        n_env: requested bond dimension D_i >= 1 along chain i (and to its parent)
+ * Bond dimensions are clamped to the largest values with D_e <= product of the
+ * other leg dimensions at both ends of every bond. */
+typedef struct {
+  int n_el;
+  const double* H_S;
+  int n_env;
+  const double* W_bar;
+  const double* rc_coupling;
+  const int* chain_len;
+  const double* const* chain_omega;
+  const double* const* chain_hop;
+  const int* local_dim;
+  const int* bond_dim;
+} ttns_problem;
+
+/* Builds one tree and its initial state (electronic state init_state, or psi_el,
+ * times the vacuum of every chain site), uploads it to device memory and
+ * computes the initial environment blocks.  *out receives the new tree. */
+ttns_status ttns_build_tree(const ttns_problem* problem, const ttns_options* opt, ttns_tree** out);
+
+/* Builds n_trees independent trees that are advanced together by one
+ * persistent launch (one cluster team per tree at a time). */
+ttns_status ttns_build_batch(int n_trees, const ttns_problem* problems, const ttns_options* opt,
+                             ttns_tree** out);
+
+/* Host-only planning: validates the problems, builds the trees and the compiled
+ * step exactly as ttns_build_* would, checks every table offset, and reports
+ * sizes without touching the GPU.  bonds[v] is the clamped bond dimension of
+ * node v of tree 0 to its parent (0 for the root). */
+typedef struct {
+  int n_nodes;
+  long long pool_complex;          /* complex elements of the state/operator pool */
+  int max_node;                    /* largest tensor (complex elements) */
+  int max_bond;                    /* largest leg dimension */
+  int instructions_per_step;
+  long long work_complex_per_worker;
+  double apply_flops_per_step;     /* useful flops of one H_eff / H_bond application of every exponential of a step */
+  double env_flops_per_step;       /* useful flops of the environment updates of a step */
+  int exponentials_per_step;
+  int env_updates_per_step;
+  int n_bonds_written;
+  int bonds[4096];
+} ttns_plan_info;
+ttns_status ttns_plan(int n_trees, const ttns_problem* problems, const ttns_options* opt, ttns_plan_info* info);
+
+/* Advances every tree by n_steps symmetric one-site TDVP steps of length dt_fs
+ * (S(dt/2) followed by its adjoint S*(dt/2)).  Asynchronous on the tree's
+ * stream; device-side failures are reported by the next synchronising call. */
+ttns_status ttns_step(ttns_tree* tree, double dt_fs, int n_steps);
+
+/* Waits for the tree's stream and returns the device status word. */
+ttns_status ttns_sync(ttns_tree* tree);
+
+/* rho_out: n_el*n_el complex, the reduced density matrix of the electronic
+ * states of tree tree_idx (Results, populations and coherences). */
+ttns_status ttns_reduced_density_matrix(ttns_tree* tree, int tree_idx, double* rho_out);
+
+/* occ_out: sum_i L_i doubles, <a^+ a> of every chain site (chains in order,
+ * sites from the reaction coordinate outward); the per-chain totals are their sums. */
+ttns_status ttns_occupations(ttns_tree* tree, int tree_idx, double* occ_out);
+
+/* norm and energy <H> (eV, with the shifted H_S) of tree tree_idx. */
+ttns_status ttns_observables(ttns_tree* tree, int tree_idx, double* norm, double* energy);
+
+/* Copies the recorded rho_S trajectory of tree tree_idx: out holds
+ * max_steps*n_el*n_el complex; *n_written receives the number of steps copied. */
+ttns_status ttns_trajectory(ttns_tree* tree, int tree_idx, double* out, int max_steps, int* n_written);
+
+/* Device-side populations of every tree (n_trees*n_el doubles, in tree order)
+ * written to dev_out on the tree's stream, without synchronising. */
+ttns_status ttns_populations_device(ttns_tree* tree, double* dev_out);
+
+/* Cumulative device counters since the build: Krylov iterations, H_eff / H_bond
+ * applications, useful contraction flops (8 per complex multiply-add of the
+ * sum-of-products terms), exponentials that hit krylov_mmax. */
+typedef struct {
+  long long krylov_iters;
+  long long applies;
+  double contraction_flops;
+  long long not_converged;
+  long long steps;
+} ttns_counters;
+ttns_status ttns_get_counters(ttns_tree* tree, ttns_counters* out);
+
+/* Node tensor access (layout: legs [parent] + [children in order] + [physical],
+ * row-major).  ttns_node_info gives the number of nodes of tree tree_idx when
+ * node < 0, else node's leg count and dims (dims: up to 8 ints). */
+ttns_status ttns_node_info(ttns_tree* tree, int tree_idx, int node, int* n_legs, int* dims, int* n_nodes);
+ttns_status ttns_get_node(ttns_tree* tree, int tree_idx, int node, double* out, size_t n_complex);
+
+/* Writes / reads a checkpoint: every tree's tensors, time and step count. */
+ttns_status ttns_save(ttns_tree* tree, const char* path);
+ttns_status ttns_load_state(ttns_tree* tree, const char* path);
+
+const char* ttns_last_error(void);
+void ttns_free(ttns_tree* tree);
+
+/* Chain maps (host, FP64).  ttns_chain_ohmic: closed form for the Ohmic density
+ * J(w) = 2 pi alpha w exp(-w/omega_c) (Laguerre weight): ||lambda|| = 2 omega_c
+ * sqrt(alpha), omega_n = omega_c (2n+2), t_n = omega_c sqrt((n+1)(n+2)).
+ * ttns_chain_from_modes: Lanczos tridiagonalisation of diag(omega) from
+ * lambda/||lambda|| with full re-orthogonalisation (L <= n_modes).
+ * Outputs: rc (1 double), onsite (L), hop (L-1), caller-owned. */
+ttns_status ttns_chain_ohmic(double alpha, double omega_c, int L, double* rc, double* onsite, double* hop);
+ttns_status ttns_chain_from_modes(int n_modes, const double* omega, const double* lambda, int L, double* rc,
+                                  double* onsite, double* hop);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTNS_H */

@@ -1,0 +1,714 @@
+// C ABI of the TTNS sweep library (declarations and contracts in include/ttns.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ttns.h"
+#include "internal.h"
+#include "model.h"
+
+namespace ttns {
+cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster, cudaStream_t stream);
+cudaError_t max_grid_for(int cluster, int* grid);
+cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double* partials,
+                           int nblocks, double* out, cudaStream_t st);
+cudaError_t launch_energy(const KernelParams& P, int node, int terms, int n2, double* partials, int nblocks,
+                          double* out, cudaStream_t st);
+cudaError_t launch_occ(const double2* dens, int d, double* out, cudaStream_t st);
+}  // namespace ttns
+
+using namespace ttns;
+
+static thread_local std::string g_err;
+
+static ttns_status fail(ttns_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+struct ttns_tree {
+  Compiled C;
+  ttns_options opt{};
+  bool batched = false;
+  int grid = 0, cluster = 16;
+  cudaStream_t stream = nullptr;
+  // device buffers
+  double2* pool = nullptr;
+  NodeDesc* d_nodes = nullptr;
+  Term* d_terms = nullptr;
+  TermList* d_lists = nullptr;
+  Factor* d_chans = nullptr;
+  Instr* d_prog = nullptr;
+  TreeDesc* d_trees = nullptr;
+  Ctl* ctl = nullptr;
+  double2* work = nullptr;
+  double* red = nullptr;
+  double* red_grid = nullptr;
+  double2* cta_scratch = nullptr;
+  int* mhist = nullptr;
+  int* traj_count = nullptr;
+  double* obs = nullptr;        // observable scratch (partials + outputs)
+  long long obs_size = 0;
+  // regions of obs (doubles)
+  long long o_bond = 0, o_site = 0, o_occ = 0, o_rho = 0, o_en = 0;
+  KernelParams P{};
+  std::vector<void*> allocs;
+  double t_fs = 0.0;
+};
+
+static const char* kStatusNames[] = {"ok", "invalid", "oom", "cuda", "not converged", "timeout", "nonfinite", "io"};
+
+extern "C" const char* ttns_last_error(void) { return g_err.c_str(); }
+
+#define CUDA_TRY(x)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (x);                                                                    \
+    if (e_ != cudaSuccess) return fail(TTNS_E_CUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+static ttns_status dalloc(ttns_tree* t, T** p, size_t count) {
+  void* q = nullptr;
+  size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TTNS_E_OOM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+  }
+  t->allocs.push_back(q);
+  *p = (T*)q;
+  return TTNS_OK;
+}
+
+template <typename T>
+static ttns_status upload(ttns_tree* t, T** p, const std::vector<T>& h) {
+  ttns_status s = dalloc(t, p, h.size());
+  if (s != TTNS_OK) return s;
+  if (!h.empty()) CUDA_TRY(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, t->stream));
+  return TTNS_OK;
+}
+
+static bool hermitian(const double* M, int n) {
+  double scale = 0;
+  for (int k = 0; k < 2 * n * n; ++k) scale = std::max(scale, std::fabs(M[k]));
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double* a = M + 2 * (i * n + j);
+      const double* b = M + 2 * (j * n + i);
+      if (std::fabs(a[0] - b[0]) > 1e-12 * (1 + scale) || std::fabs(a[1] + b[1]) > 1e-12 * (1 + scale)) return false;
+    }
+  return true;
+}
+
+static ttns_status validate(const ttns_problem* p, const ttns_options* opt, TreeInput* in) {
+  if (!p) return fail(TTNS_E_INVALID, "problem is NULL");
+  if (p->n_el < 1 || p->n_el > TTNS_MAX_D) return fail(TTNS_E_INVALID, "n_el out of range");
+  if (!p->H_S || !p->W_bar || !p->rc_coupling || !p->chain_len || !p->chain_omega || !p->local_dim || !p->bond_dim)
+    return fail(TTNS_E_INVALID, "NULL array in problem");
+  if (p->n_env < 1 || p->n_env > 64) return fail(TTNS_E_INVALID, "n_env out of range");
+  const int er = opt ? opt->er_tree : 0;
+  if (er && (p->n_env < 2 || (p->n_env & (p->n_env - 1)) != 0))
+    return fail(TTNS_E_INVALID, "er_tree needs a power-of-two number of environments >= 2");
+  if (er && (opt->D_er < 1 || opt->D_er > TTNS_MAX_D)) return fail(TTNS_E_INVALID, "D_er out of range");
+  const int ne = p->n_el;
+  if (!hermitian(p->H_S, ne)) return fail(TTNS_E_INVALID, "H_S is not Hermitian");
+  in->n_el = ne;
+  in->n_env = p->n_env;
+  in->H_S.resize(ne * ne);
+  for (int k = 0; k < ne * ne; ++k) in->H_S[k] = cplx(p->H_S[2 * k], p->H_S[2 * k + 1]);
+  for (int i = 0; i < p->n_env; ++i) {
+    const double* W = p->W_bar + (size_t)2 * ne * ne * i;
+    if (!hermitian(W, ne)) return fail(TTNS_E_INVALID, "W_bar[" + std::to_string(i) + "] is not Hermitian");
+    std::vector<cplx> w(ne * ne);
+    for (int k = 0; k < ne * ne; ++k) w[k] = cplx(W[2 * k], W[2 * k + 1]);
+    in->W.push_back(w);
+    const int L = p->chain_len[i], d = p->local_dim[i], D = p->bond_dim[i];
+    if (L < 1 || L > 4096) return fail(TTNS_E_INVALID, "chain_len out of range");
+    if (d < 2 || d > TTNS_MAX_D) return fail(TTNS_E_INVALID, "local_dim out of range (2..64)");
+    if (D < 1) return fail(TTNS_E_INVALID, "bond_dim must be >= 1");
+    if (!std::isfinite(p->rc_coupling[i])) return fail(TTNS_E_INVALID, "rc_coupling not finite");
+    if (!p->chain_omega[i]) return fail(TTNS_E_INVALID, "chain_omega entry is NULL");
+    if (L > 1 && (!p->chain_hop || !p->chain_hop[i])) return fail(TTNS_E_INVALID, "chain_hop entry is NULL");
+    in->rc.push_back(p->rc_coupling[i]);
+    in->omega.emplace_back(p->chain_omega[i], p->chain_omega[i] + L);
+    if (L > 1)
+      in->hop.emplace_back(p->chain_hop[i], p->chain_hop[i] + (L - 1));
+    else
+      in->hop.emplace_back();
+    in->L.push_back(L);
+    in->d.push_back(d);
+    in->D.push_back(std::min(D, TTNS_MAX_D));
+  }
+  in->er_tree = er;
+  in->D_er = er ? opt->D_er : 0;
+  in->psi_el.assign(ne, cplx(0, 0));
+  if (opt && opt->psi_el) {
+    double nn = 0;
+    for (int s = 0; s < ne; ++s) {
+      in->psi_el[s] = cplx(opt->psi_el[2 * s], opt->psi_el[2 * s + 1]);
+      nn += std::norm(in->psi_el[s]);
+    }
+    if (!(nn > 0) || !std::isfinite(nn)) return fail(TTNS_E_INVALID, "psi_el is zero or not finite");
+  } else {
+    const int s0 = opt ? opt->init_state : 0;
+    if (s0 < 0 || s0 >= ne) return fail(TTNS_E_INVALID, "init_state out of range");
+    in->psi_el[s0] = 1.0;
+  }
+  return TTNS_OK;
+}
+
+// Checks every offset of the compiled tables against the buffers they index, so that a
+// malformed table is reported on the host instead of reaching the device.
+static ttns_status check_tables(const Compiled& C, int mmax, long long kvec, long long per_cta, int n_tmp) {
+  auto in_pool = [&](long long off, long long n) { return off >= 0 && n >= 0 && off + n <= C.pool_size; };
+  for (size_t i = 0; i < C.nodes.size(); ++i) {
+    const NodeDesc& nd = C.nodes[i];
+    if (nd.nl < 1 || nd.nl > TTNS_MAX_LEGS) return fail(TTNS_E_INVALID, "table: leg count");
+    long long sz = 1;
+    for (int k = 0; k < nd.nl; ++k) {
+      if (nd.dims[k] < 1 || nd.dims[k] > TTNS_MAX_D) return fail(TTNS_E_INVALID, "table: dim out of range");
+      sz *= nd.dims[k];
+    }
+    if (sz != nd.size || !in_pool(nd.off, nd.size) || nd.size > kvec) return fail(TTNS_E_INVALID, "table: node extent");
+  }
+  auto check_factor = [&](const Factor& f, const NodeDesc& nd) {
+    if (f.leg < 0 || f.leg >= nd.nl) return false;
+    const long long D = nd.dims[f.leg];
+    return in_pool(f.mat, D * D);
+  };
+  for (const Instr& I : C.prog) {
+    if (I.node < 0 || I.node >= (int)C.nodes.size()) return fail(TTNS_E_INVALID, "table: instruction node");
+    if (I.tree < 0 || I.tree >= (int)C.trees.size()) return fail(TTNS_E_INVALID, "table: instruction tree");
+    const NodeDesc& nd = C.nodes[I.node];
+    const TreeDesc& td = C.trees[I.tree];
+    if (!in_pool(td.bond_off, (long long)TTNS_MAX_D * TTNS_MAX_D)) return fail(TTNS_E_INVALID, "table: bond buffer");
+    if (I.op == OP_FWD || I.op == OP_BOND || I.op == OP_ENV) {
+      if (I.terms < 0 || I.terms >= (int)C.lists.size()) return fail(TTNS_E_INVALID, "table: term list");
+      const TermList& L = C.lists[I.terms];
+      if (L.first < 0 || L.first + L.count > (int)C.terms.size() || L.n2 > n_tmp || L.n2 > L.count)
+        return fail(TTNS_E_INVALID, "table: term range");
+      for (int k = 0; k < L.count; ++k) {
+        const Term& T = C.terms[L.first + k];
+        const bool two = k >= L.count - L.n2;
+        if (T.nf != (two ? 2 : 1)) return fail(TTNS_E_INVALID, "table: term order");
+        for (int j = 0; j < T.nf; ++j)
+          if (!check_factor(T.f[j], nd)) return fail(TTNS_E_INVALID, "table: factor");
+      }
+      if (I.op != OP_ENV && (I.hist < 0 || I.hist >= std::max(C.n_hist, 1))) return fail(TTNS_E_INVALID, "table: hist");
+    }
+    if (I.op == OP_ENV) {
+      if (I.leg < 0 || I.leg >= nd.nl || I.D != nd.dims[I.leg]) return fail(TTNS_E_INVALID, "table: env leg");
+      if (I.chan_first < 0 || I.chan_first + I.nchan > (int)C.chans.size()) return fail(TTNS_E_INVALID, "table: chans");
+      for (int b = 0; b < I.nchan; ++b)
+        if (!check_factor(C.chans[I.chan_first + b], nd)) return fail(TTNS_E_INVALID, "table: channel factor");
+      if (!in_pool(I.env_out, (long long)(1 + I.nchan) * I.D * I.D)) return fail(TTNS_E_INVALID, "table: env out");
+      if (1 + I.nchan > mmax || 2LL * (1 + I.nchan) * I.D * I.D > per_cta) return fail(TTNS_E_INVALID, "table: env size");
+    }
+    if (I.op == OP_QR || I.op == OP_ABSORB) {
+      if (I.leg < 0 || I.leg >= nd.nl || I.D != nd.dims[I.leg]) return fail(TTNS_E_INVALID, "table: qr leg");
+      if (nd.size / I.D < I.D) return fail(TTNS_E_INVALID, "table: qr needs rows >= cols");
+      if (2LL * I.D * I.D > per_cta) return fail(TTNS_E_INVALID, "table: qr partials");
+    }
+    if (I.op == OP_BOND) {
+      if (nd.off != td.bond_off || nd.nl != 2) return fail(TTNS_E_INVALID, "table: bond node");
+    }
+    if (I.op == OP_RECORD) {
+      if (td.n_el * td.n_el * 2LL > per_cta) return fail(TTNS_E_INVALID, "table: record partials");
+      if (td.traj_off >= 0 && !in_pool(td.traj_off, 0)) return fail(TTNS_E_INVALID, "table: trajectory");
+    }
+  }
+  return TTNS_OK;
+}
+
+struct Sizes {
+  int mmax;
+  long long kvec, work_stride, per_cta;
+  int maxchan;
+};
+
+static ttns_status plan_sizes(const Compiled& C, const ttns_options& o, Sizes* z) {
+  z->mmax = std::min(o.krylov_mmax > 0 ? o.krylov_mmax : 30, TTNS_KMAX);
+  z->maxchan = 0;
+  for (const Instr& I : C.prog) z->maxchan = std::max(z->maxchan, I.nchan);
+  if (1 + z->maxchan > z->mmax) return fail(TTNS_E_INVALID, "too many coupling channels for krylov_mmax");
+  if (C.max_D > TTNS_MAX_D) return fail(TTNS_E_INVALID, "a bond dimension exceeds 64");
+  z->kvec = ((long long)C.max_node + 31) / 32 * 32;
+  z->work_stride = (long long)(z->mmax + std::max(C.max_tmp, 1) + 2) * z->kvec;
+  long long per_cta = 8;
+  per_cta = std::max<long long>(per_cta, 2LL * C.max_D * C.max_D);
+  per_cta = std::max<long long>(per_cta, 2LL * (1 + z->maxchan) * C.max_D * C.max_D);
+  per_cta = std::max<long long>(per_cta, 2LL * TTNS_MAX_D);
+  z->per_cta = per_cta;
+  return check_tables(C, z->mmax, z->kvec, per_cta, std::max(C.max_tmp, 1));
+}
+
+static ttns_status device_init(ttns_tree* t) {
+  Compiled& C = t->C;
+  const ttns_options& o = t->opt;
+  Sizes z;
+  ttns_status s = plan_sizes(C, o, &z);
+  if (s != TTNS_OK) return s;
+  const int mmax = z.mmax;
+  const long long kvec = z.kvec, work_stride = z.work_stride, per_cta = z.per_cta;
+  t->cluster = o.cluster_ctas > 0 ? o.cluster_ctas : 16;
+  if (t->cluster > 16) return fail(TTNS_E_INVALID, "cluster_ctas must be <= 16");
+  int maxgrid = 0;
+  CUDA_TRY(max_grid_for(t->cluster, &maxgrid));
+  if (maxgrid < t->cluster) return fail(TTNS_E_CUDA, "no co-resident cluster of the requested size");
+  int grid = o.grid_ctas > 0 ? o.grid_ctas : maxgrid;
+  grid = std::min(grid, maxgrid);
+  grid = (grid / t->cluster) * t->cluster;
+  if (grid < t->cluster) grid = t->cluster;
+  t->grid = grid;
+  const int n_clusters = grid / t->cluster;
+  const int n_workers = t->batched ? n_clusters : 1;
+  if ((s = dalloc(t, &t->pool, C.pool_size)) != TTNS_OK) return s;
+  CUDA_TRY(cudaMemcpyAsync(t->pool, C.pool_init.data(), C.pool_size * sizeof(double2), cudaMemcpyHostToDevice, t->stream));
+  if ((s = upload(t, &t->d_nodes, C.nodes)) != TTNS_OK) return s;
+  if ((s = upload(t, &t->d_terms, C.terms)) != TTNS_OK) return s;
+  if ((s = upload(t, &t->d_lists, C.lists)) != TTNS_OK) return s;
+  if ((s = upload(t, &t->d_chans, C.chans)) != TTNS_OK) return s;
+  if ((s = upload(t, &t->d_prog, C.prog)) != TTNS_OK) return s;
+  if ((s = upload(t, &t->d_trees, C.trees)) != TTNS_OK) return s;
+  if ((s = dalloc(t, &t->ctl, 1)) != TTNS_OK) return s;
+  CUDA_TRY(cudaMemsetAsync(t->ctl, 0, sizeof(Ctl), t->stream));
+  if ((s = dalloc(t, &t->work, (size_t)n_workers * work_stride)) != TTNS_OK) return s;
+  CUDA_TRY(cudaMemsetAsync(t->work, 0, (size_t)n_workers * work_stride * sizeof(double2), t->stream));
+  const long long red_stride = (long long)t->cluster * per_cta;
+  if ((s = dalloc(t, &t->red, (size_t)n_clusters * 2 * red_stride)) != TTNS_OK) return s;
+  const long long red_stride_grid = (long long)grid * per_cta;
+  if ((s = dalloc(t, &t->red_grid, (size_t)2 * red_stride_grid)) != TTNS_OK) return s;
+  const long long scr = 3LL * TTNS_MAX_D * TTNS_MAX_D;
+  if ((s = dalloc(t, &t->cta_scratch, (size_t)grid * scr)) != TTNS_OK) return s;
+  if ((s = dalloc(t, &t->mhist, std::max(C.n_hist, 1))) != TTNS_OK) return s;
+  CUDA_TRY(cudaMemsetAsync(t->mhist, 0, std::max(C.n_hist, 1) * sizeof(int), t->stream));
+  if ((s = dalloc(t, &t->traj_count, C.trees.size())) != TTNS_OK) return s;
+  CUDA_TRY(cudaMemsetAsync(t->traj_count, 0, C.trees.size() * sizeof(int), t->stream));
+  // observables scratch: partials for up to 1024 blocks of 2*maxD^2 doubles + densities per node
+  const long long nn = (long long)C.nodes.size();
+  const long long d2 = 2LL * C.max_D * C.max_D;
+  t->o_bond = 1024LL * d2;
+  t->o_site = t->o_bond + nn * d2;
+  t->o_occ = t->o_site + nn * d2;
+  t->o_rho = t->o_occ + nn + 64;
+  t->o_en = t->o_rho + 2 * 64 * 64;
+  t->obs_size = t->o_en + 16;
+  if ((s = dalloc(t, &t->obs, t->obs_size)) != TTNS_OK) return s;
+
+  KernelParams& P = t->P;
+  P.pool = t->pool;
+  P.nodes = t->d_nodes;
+  P.terms = t->d_terms;
+  P.lists = t->d_lists;
+  P.chans = t->d_chans;
+  P.prog = t->d_prog;
+  P.trees = t->d_trees;
+  P.n_trees = (int)C.trees.size();
+  P.batched = t->batched ? 1 : 0;
+  P.ctl = t->ctl;
+  P.work = t->work;
+  P.work_stride = work_stride;
+  P.kvec = (int)kvec;
+  P.n_tmp = std::max(C.max_tmp, 1);
+  P.red = t->red;
+  P.red_stride = red_stride;
+  P.red_grid = t->red_grid;
+  P.red_stride_grid = red_stride_grid;
+  P.cta_scratch = t->cta_scratch;
+  P.cta_scratch_stride = scr;
+  P.mhist = t->mhist;
+  P.traj_count = t->traj_count;
+  P.max_record = o.max_record > 0 ? o.max_record : 4096;
+  P.record = o.record;
+  P.dt = 0.0;
+  P.n_steps = 1;
+  P.precision = o.precision;
+  P.tol = o.krylov_tol > 0 ? o.krylov_tol : 1e-12;
+  P.mmax = mmax;
+  P.cluster_ctas = t->cluster;
+  P.spin_limit = 20LL * 1000 * 1000 * 1000;  // clock cycles (~10 s)
+  // initial environment pass
+  CUDA_TRY(launch_sweep(P, 0, t->grid, t->cluster, t->stream));
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  Ctl h;
+  CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  if (h.status != 0) return fail((ttns_status)h.status, std::string("device status after the initial pass: ") + kStatusNames[h.status]);
+  return TTNS_OK;
+}
+
+static ttns_status compile_only(int n_trees, const ttns_problem* probs, const ttns_options* opt, ttns_tree* t) {
+  ttns_options o{};
+  if (opt) o = *opt;
+  if (o.precision != TTNS_FP64 && o.precision != TTNS_MIXED) return fail(TTNS_E_INVALID, "unknown precision");
+  if (o.krylov_mmax < 0 || o.krylov_mmax > TTNS_KMAX) return fail(TTNS_E_INVALID, "krylov_mmax out of range (0..32)");
+  if (o.krylov_tol < 0) return fail(TTNS_E_INVALID, "krylov_tol < 0");
+  if (o.max_record < 0) return fail(TTNS_E_INVALID, "max_record < 0");
+  std::vector<TreeInput> ins(n_trees);
+  for (int i = 0; i < n_trees; ++i) {
+    ttns_status s = validate(&probs[i], &o, &ins[i]);
+    if (s != TTNS_OK) return s;
+  }
+  t->opt = o;
+  t->opt.psi_el = nullptr;
+  t->batched = n_trees > 1;
+  t->stream = (cudaStream_t)o.cuda_stream;
+  try {
+    t->C = compile_trees(ins, t->batched, /*grid_threshold=*/65536, o.max_record > 0 ? o.max_record : 4096, o.record);
+  } catch (const std::exception& e) {
+    return fail(TTNS_E_INVALID, std::string("model: ") + e.what());
+  }
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_plan(int n_trees, const ttns_problem* problems, const ttns_options* opt,
+                                 ttns_plan_info* info) {
+  if (!info) return fail(TTNS_E_INVALID, "info is NULL");
+  if (n_trees < 1 || !problems) return fail(TTNS_E_INVALID, "no problems");
+  ttns_tree t;
+  ttns_status s = compile_only(n_trees, problems, opt, &t);
+  if (s != TTNS_OK) return s;
+  Sizes z;
+  if ((s = plan_sizes(t.C, t.opt, &z)) != TTNS_OK) return s;
+  std::memset(info, 0, sizeof(*info));
+  info->n_nodes = 0;
+  for (const TreeDesc& td : t.C.trees) info->n_nodes += td.n_nodes;
+  info->pool_complex = t.C.pool_size;
+  info->max_node = t.C.max_node;
+  info->max_bond = t.C.max_D;
+  info->instructions_per_step = 0;
+  for (const TreeDesc& td : t.C.trees) info->instructions_per_step += td.prog_count;
+  info->work_complex_per_worker = z.work_stride;
+  const HostTree& h = t.C.host[0];
+  for (int v = 0; v < h.n() && v < 4096; ++v) info->bonds[v] = h.bond[v];
+  info->n_bonds_written = std::min(h.n(), 4096);
+  // useful flops of one step if every exponential took one Krylov iteration (scale by the counted iterations)
+  double fexp = 0, fenv = 0;
+  long long nexp = 0, nenv = 0;
+  for (const Instr& I : t.C.prog) {
+    if (I.op == OP_FWD || I.op == OP_BOND) { fexp += I.flops; ++nexp; }
+    if (I.op == OP_ENV) { fenv += I.flops; ++nenv; }
+  }
+  info->apply_flops_per_step = fexp;
+  info->env_flops_per_step = fenv;
+  info->exponentials_per_step = nexp;
+  info->env_updates_per_step = nenv;
+  return TTNS_OK;
+}
+
+static ttns_status build(int n_trees, const ttns_problem* probs, const ttns_options* opt, ttns_tree** out) {
+  if (!out) return fail(TTNS_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_trees < 1 || !probs) return fail(TTNS_E_INVALID, "no problems");
+  ttns_tree* t = new ttns_tree();
+  {
+    ttns_status s0 = compile_only(n_trees, probs, opt, t);
+    if (s0 != TTNS_OK) {
+      delete t;
+      return s0;
+    }
+  }
+  ttns_status s = device_init(t);
+  if (s != TTNS_OK) {
+    std::string keep = g_err;
+    ttns_free(t);
+    g_err = keep;
+    return s;
+  }
+  *out = t;
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_build_tree(const ttns_problem* problem, const ttns_options* opt, ttns_tree** out) {
+  return build(1, problem, opt, out);
+}
+
+extern "C" ttns_status ttns_build_batch(int n_trees, const ttns_problem* problems, const ttns_options* opt,
+                                        ttns_tree** out) {
+  return build(n_trees, problems, opt, out);
+}
+
+extern "C" ttns_status ttns_step(ttns_tree* t, double dt_fs, int n_steps) {
+  if (!t) return fail(TTNS_E_INVALID, "tree is NULL");
+  if (n_steps < 0) return fail(TTNS_E_INVALID, "n_steps < 0");
+  if (!std::isfinite(dt_fs)) return fail(TTNS_E_INVALID, "dt not finite");
+  if (n_steps == 0) return TTNS_OK;
+  t->P.dt = dt_fs;
+  t->P.n_steps = n_steps;
+  CUDA_TRY(launch_sweep(t->P, 1, t->grid, t->cluster, t->stream));
+  t->t_fs += dt_fs * n_steps;
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_sync(ttns_tree* t) {
+  if (!t) return fail(TTNS_E_INVALID, "tree is NULL");
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  Ctl h;
+  CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  if (h.status != 0)
+    return fail((ttns_status)h.status, std::string("device status: ") + kStatusNames[h.status] + " (op " +
+                                           std::to_string(h.err_where) + ", node " + std::to_string(h.err_node) + ")");
+  return TTNS_OK;
+}
+
+static int find_root_fwd_terms(ttns_tree* t, int tree_idx, int* n2) {
+  const TreeDesc& td = t->C.trees[tree_idx];
+  for (int k = 0; k < td.prog_count; ++k) {
+    const Instr& I = t->C.prog[td.prog_first + k];
+    if (I.op == OP_FWD && I.node == td.node0) {
+      *n2 = t->C.lists[I.terms].n2;
+      return I.terms;
+    }
+  }
+  return -1;
+}
+
+// root densities: rho_S (phys leg) into obs + off
+static ttns_status density(ttns_tree* t, int node, int leg, const double2* rho_in, double* out) {
+  const NodeDesc& nd = t->C.nodes[node];
+  const int D = nd.dims[leg];
+  int nblocks = (int)std::min<long long>(1024, std::max<long long>(1, nd.size / D / 64));
+  CUDA_TRY(launch_density(t->pool, nd, leg, rho_in, t->obs, nblocks, out, t->stream));
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_reduced_density_matrix(ttns_tree* t, int tree_idx, double* rho_out) {
+  if (!t || !rho_out) return fail(TTNS_E_INVALID, "NULL argument");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  const TreeDesc& td = t->C.trees[tree_idx];
+  double* out = t->obs + t->o_rho;
+  if ((s = density(t, td.node0, td.root_phys_leg, nullptr, out)) != TTNS_OK) return s;
+  CUDA_TRY(cudaMemcpyAsync(rho_out, out, sizeof(double) * 2 * td.n_el * td.n_el, cudaMemcpyDeviceToHost, t->stream));
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_occupations(ttns_tree* t, int tree_idx, double* occ_out) {
+  if (!t || !occ_out) return fail(TTNS_E_INVALID, "NULL argument");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  const HostTree& h = t->C.host[tree_idx];
+  const TreeDesc& td = t->C.trees[tree_idx];
+  const int maxD = t->C.max_D;
+  // per node: incoming parent-bond density at dens + v * 2 maxD^2
+  double* dens = t->obs + t->o_bond;
+  double* occ_dev = t->obs + t->o_occ;
+  // preorder walk
+  std::vector<int> order;
+  std::vector<int> stack{0};
+  while (!stack.empty()) {
+    int v = stack.back();
+    stack.pop_back();
+    order.push_back(v);
+    for (auto it = h.children[v].rbegin(); it != h.children[v].rend(); ++it) stack.push_back(*it);
+  }
+  std::vector<int> site_pos(h.n(), -1);
+  {
+    int k = 0;
+    for (auto& c : h.chain_nodes)
+      for (int v : c) site_pos[v] = k++;
+  }
+  double* site_dens = t->obs + t->o_site;  // 2*maxD^2 per site
+  for (int v : order) {
+    const int gv = td.node0 + v;
+    const double2* rin = h.parent[v] >= 0 ? (const double2*)(dens + (long long)v * 2 * maxD * maxD) : nullptr;
+    for (int c : h.children[v]) {
+      if ((s = density(t, gv, h.leg_of(v, c), rin, dens + (long long)c * 2 * maxD * maxD)) != TTNS_OK) return s;
+    }
+    if (h.parent[v] >= 0 && h.phys[v] > 0 && site_pos[v] >= 0) {
+      double* sd = site_dens + (long long)site_pos[v] * 2 * maxD * maxD;
+      if ((s = density(t, gv, h.phys_leg(v), rin, sd)) != TTNS_OK) return s;
+      CUDA_TRY(launch_occ((const double2*)sd, h.phys[v], occ_dev + site_pos[v], t->stream));
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(occ_out, occ_dev, sizeof(double) * td.n_sites, cudaMemcpyDeviceToHost, t->stream));
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_observables(ttns_tree* t, int tree_idx, double* norm, double* energy) {
+  if (!t || !norm || !energy) return fail(TTNS_E_INVALID, "NULL argument");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  if (t->batched) {
+    // the temporaries of worker 0 are used: fine outside a sweep
+  }
+  int n2 = 0;
+  int li = find_root_fwd_terms(t, tree_idx, &n2);
+  if (li < 0) return fail(TTNS_E_INVALID, "no root operator");
+  double* out = t->obs + t->o_en;
+  const int nb = 256;
+  CUDA_TRY(launch_energy(t->P, t->C.trees[tree_idx].node0, li, n2, t->obs, nb, out, t->stream));
+  double h[2];
+  CUDA_TRY(cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, t->stream));
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  *norm = std::sqrt(h[1]);
+  *energy = h[1] > 0 ? h[0] / h[1] : 0.0;
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_trajectory(ttns_tree* t, int tree_idx, double* out, int max_steps, int* n_written) {
+  if (!t || !out || !n_written) return fail(TTNS_E_INVALID, "NULL argument");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  if (!t->opt.record) return fail(TTNS_E_INVALID, "the tree was built without record=1");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  int cnt = 0;
+  CUDA_TRY(cudaMemcpy(&cnt, t->traj_count + tree_idx, sizeof(int), cudaMemcpyDeviceToHost));
+  const TreeDesc& td = t->C.trees[tree_idx];
+  cnt = std::min(cnt, std::min(max_steps, t->P.max_record));
+  if (cnt > 0)
+    CUDA_TRY(cudaMemcpy(out, t->pool + td.traj_off, sizeof(double2) * (size_t)cnt * td.n_el * td.n_el,
+                        cudaMemcpyDeviceToHost));
+  *n_written = cnt;
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_populations_device(ttns_tree* t, double* dev_out) {
+  if (!t || !dev_out) return fail(TTNS_E_INVALID, "NULL argument");
+  ttns_status s;
+  int off = 0;
+  for (size_t k = 0; k < t->C.trees.size(); ++k) {
+    const TreeDesc& td = t->C.trees[k];
+    double* tmp = t->obs + t->o_rho;
+    if ((s = density(t, td.node0, td.root_phys_leg, nullptr, tmp)) != TTNS_OK) return s;
+    // diagonal (real parts) -> dev_out
+    for (int q = 0; q < td.n_el; ++q)
+      CUDA_TRY(cudaMemcpyAsync(dev_out + off + q, tmp + 2 * (q * td.n_el + q), sizeof(double), cudaMemcpyDeviceToDevice,
+                               t->stream));
+    off += td.n_el;
+  }
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_get_counters(ttns_tree* t, ttns_counters* out) {
+  if (!t || !out) return fail(TTNS_E_INVALID, "NULL argument");
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  Ctl h;
+  CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  out->krylov_iters = (long long)h.krylov_iters;
+  out->applies = (long long)h.applies;
+  out->contraction_flops = h.flops;
+  out->not_converged = (long long)h.not_converged;
+  out->steps = (long long)h.steps;
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_node_info(ttns_tree* t, int tree_idx, int node, int* n_legs, int* dims, int* n_nodes) {
+  if (!t) return fail(TTNS_E_INVALID, "tree is NULL");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  const TreeDesc& td = t->C.trees[tree_idx];
+  if (n_nodes) *n_nodes = td.n_nodes;
+  if (node < 0) return TTNS_OK;
+  if (node >= td.n_nodes) return fail(TTNS_E_INVALID, "node out of range");
+  const NodeDesc& nd = t->C.nodes[td.node0 + node];
+  if (n_legs) *n_legs = nd.nl;
+  if (dims)
+    for (int k = 0; k < nd.nl; ++k) dims[k] = nd.dims[k];
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_get_node(ttns_tree* t, int tree_idx, int node, double* out, size_t n_complex) {
+  if (!t || !out) return fail(TTNS_E_INVALID, "NULL argument");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  const TreeDesc& td = t->C.trees[tree_idx];
+  if (node < 0 || node >= td.n_nodes) return fail(TTNS_E_INVALID, "node out of range");
+  const NodeDesc& nd = t->C.nodes[td.node0 + node];
+  if (n_complex < (size_t)nd.size) return fail(TTNS_E_INVALID, "output buffer too small");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  CUDA_TRY(cudaMemcpy(out, t->pool + nd.off, sizeof(double2) * nd.size, cudaMemcpyDeviceToHost));
+  return TTNS_OK;
+}
+
+static const char kMagic[8] = {'T', 'T', 'N', 'S', 'C', 'K', 'P', '1'};
+
+extern "C" ttns_status ttns_save(ttns_tree* t, const char* path) {
+  if (!t || !path) return fail(TTNS_E_INVALID, "NULL argument");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  std::vector<double2> pool(t->C.pool_size);
+  std::vector<int> mh(std::max(t->C.n_hist, 1)), tc(t->C.trees.size());
+  Ctl h;
+  CUDA_TRY(cudaMemcpy(pool.data(), t->pool, pool.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(mh.data(), t->mhist, mh.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(tc.data(), t->traj_count, tc.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(TTNS_E_IO, std::string("cannot open ") + path);
+  long long hdr[4] = {(long long)pool.size(), (long long)mh.size(), (long long)tc.size(), 0};
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
+            std::fwrite(&t->t_fs, sizeof(double), 1, f) == 1 &&
+            std::fwrite(pool.data(), sizeof(double2), pool.size(), f) == pool.size() &&
+            std::fwrite(mh.data(), sizeof(int), mh.size(), f) == mh.size() &&
+            std::fwrite(tc.data(), sizeof(int), tc.size(), f) == tc.size() && std::fwrite(&h, sizeof(Ctl), 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(TTNS_E_IO, std::string("write failed: ") + path);
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_load_state(ttns_tree* t, const char* path) {
+  if (!t || !path) return fail(TTNS_E_INVALID, "NULL argument");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(TTNS_E_IO, std::string("cannot open ") + path);
+  char magic[8];
+  long long hdr[4];
+  double tf = 0;
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+            std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(&tf, sizeof(double), 1, f) == 1;
+  if (!ok || hdr[0] != t->C.pool_size || hdr[1] != (long long)std::max(t->C.n_hist, 1) ||
+      hdr[2] != (long long)t->C.trees.size()) {
+    std::fclose(f);
+    return fail(TTNS_E_IO, "checkpoint does not match this tree (or is truncated)");
+  }
+  std::vector<double2> pool(hdr[0]);
+  std::vector<int> mh(hdr[1]), tc(hdr[2]);
+  Ctl h;
+  ok = std::fread(pool.data(), sizeof(double2), pool.size(), f) == pool.size() &&
+       std::fread(mh.data(), sizeof(int), mh.size(), f) == mh.size() &&
+       std::fread(tc.data(), sizeof(int), tc.size(), f) == tc.size() && std::fread(&h, sizeof(Ctl), 1, f) == 1;
+  std::fclose(f);
+  if (!ok) return fail(TTNS_E_IO, "checkpoint truncated");
+  h.bar_count = 0;
+  h.bar_gen = 0;
+  h.status = 0;
+  CUDA_TRY(cudaMemcpy(t->pool, pool.data(), pool.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->mhist, mh.data(), mh.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->traj_count, tc.data(), tc.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
+  t->t_fs = tf;
+  return TTNS_OK;
+}
+
+extern "C" void ttns_free(ttns_tree* t) {
+  if (!t) return;
+  if (t->stream) cudaStreamSynchronize(t->stream); else cudaDeviceSynchronize();
+  for (void* p : t->allocs) cudaFree(p);
+  delete t;
+}
+
+extern "C" ttns_status ttns_chain_ohmic(double alpha, double omega_c, int L, double* rc, double* onsite, double* hop) {
+  if (L < 1 || !rc || !onsite || (L > 1 && !hop)) return fail(TTNS_E_INVALID, "bad arguments");
+  if (!(alpha >= 0) || !(omega_c > 0)) return fail(TTNS_E_INVALID, "alpha must be >= 0 and omega_c > 0");
+  chain_ohmic(alpha, omega_c, L, rc, onsite, hop);
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_chain_from_modes(int n_modes, const double* omega, const double* lambda, int L, double* rc,
+                                             double* onsite, double* hop) {
+  if (n_modes < 1 || !omega || !lambda || !rc || !onsite || (L > 1 && !hop)) return fail(TTNS_E_INVALID, "bad arguments");
+  if (L < 1 || L > n_modes) return fail(TTNS_E_INVALID, "L must be in 1..n_modes");
+  if (!chain_from_modes(n_modes, omega, lambda, L, rc, onsite, hop))
+    return fail(TTNS_E_INVALID, "Lanczos breakdown: fewer distinct modes than sites");
+  return TTNS_OK;
+}

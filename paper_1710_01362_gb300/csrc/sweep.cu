@@ -1,0 +1,1111 @@
+// Device side of the TTNS sweep: one persistent cooperative kernel that runs the
+// compiled one-site TDVP step (Results, "TTNS for vibronic quantum dynamics":
+// every tensor evolved in turn with its local effective Hamiltonian) for n steps.
+//
+// Execution model (GB300: 152 SMs, FP64 at 1/64 of the FP32 rate with a long
+// dependent latency, hardware cluster barriers ~0.2 us, software grid barriers
+// ~2.3 us):
+//   * a "team" executes one instruction: either one thread-block cluster
+//     (hardware barrier; used for every node of small trees and for chain sites)
+//     or the whole grid (software barrier; used for the large electronic root);
+//   * in batched mode every cluster advances its own trees independently;
+//   * reductions are deterministic: per-CTA partials, then a fixed-order sum
+//     that every CTA computes identically (no floating-point atomics);
+//   * every spin-wait is bounded and reports TTNS_E_TIMEOUT instead of hanging.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace ttns {
+
+#define NT 256
+#define NWARP (NT / 32)
+#define HBAR_EVFS 0.6582119569
+#define QR_NULL_REL 1e-8
+
+// status codes mirrored from ttns.h
+#define ST_TIMEOUT 5
+#define ST_NOT_CONVERGED 4
+#define ST_NONFINITE 6
+
+__constant__ double c_inv[256];       // 1/n, c_inv[0] = 0
+__constant__ double c_invfact[128];   // 1/n!
+
+// ------------------------------------------------------------------ complex helpers
+template <typename T> struct C2;
+template <> struct C2<double> { using t = double2; };
+template <> struct C2<float> { using t = float2; };
+
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t ld(const double2* p) {
+  double2 v = *p;
+  typename C2<T>::t r;
+  r.x = (T)v.x;
+  r.y = (T)v.y;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void cmac(typename C2<T>::t& acc, typename C2<T>::t a, typename C2<T>::t b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// ------------------------------------------------------------------ teams
+struct Team {
+  int kind;      // TEAM_GRID / TEAM_CLUSTER
+  int rank;      // CTA rank in the team
+  int size;      // CTAs in the team
+  double* red;   // two partial buffers, red_stride doubles each
+  long long red_stride;
+  int parity;
+  Ctl* ctl;
+  long long spin_limit;
+  __device__ int nthr() const { return size * NT; }
+  __device__ int gtid() const { return rank * NT + (int)threadIdx.x; }
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_volatile_int(const int* p) { return *(volatile const int*)p; }
+
+__device__ void set_status(Ctl* ctl, int st, int where, int node) {
+  if (atomicCAS(&ctl->status, 0, st) == 0) {
+    ctl->err_where = where;
+    ctl->err_node = node;
+  }
+}
+
+// software barrier over all CTAs of the grid; bounded
+__device__ void grid_sync(Ctl* ctl, long long spin_limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned g = ld_acquire(&ctl->bar_gen);
+    __threadfence();
+    unsigned prev = atomicAdd(&ctl->bar_count, 1u);
+    if (prev == gridDim.x - 1) {
+      atomicExch(&ctl->bar_count, 0u);
+      __threadfence();
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&ctl->bar_gen), "r"(g + 1) : "memory");
+    } else {
+      long long t0 = clock64();
+      while (ld_acquire(&ctl->bar_gen) == g) {
+        if (ld_volatile_int(&ctl->status) != 0) break;
+        if (clock64() - t0 > spin_limit) {
+          set_status(ctl, ST_TIMEOUT, 100, -1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void team_sync(Team& tm) {
+  if (tm.kind == TEAM_CLUSTER) {
+    cg::this_cluster().sync();
+  } else {
+    grid_sync(tm.ctl, tm.spin_limit);
+  }
+}
+
+// warp sum with a fixed order; every lane returns lane 0's value
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+// All-reduce of nv (<= 8) per-thread values over the team.  Deterministic and
+// identical on every CTA.  Contains one team barrier.
+__device__ void team_allreduce(Team& tm, double* v, int nv) {
+  __shared__ double s_w[NWARP * 8];
+  __shared__ double s_out[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < nv; ++i) {
+    double s = warp_sum(v[i]);
+    if (lane == 0) s_w[warp * 8 + i] = s;
+  }
+  __syncthreads();
+  double* buf = tm.red + (long long)tm.parity * tm.red_stride;
+  if (threadIdx.x < nv) {
+    double s = 0;
+    for (int w = 0; w < NWARP; ++w) s += s_w[w * 8 + threadIdx.x];
+    buf[tm.rank * 8 + threadIdx.x] = s;
+  }
+  team_sync(tm);
+  if (warp == 0) {
+    for (int i = 0; i < nv; ++i) {
+      double s = 0;
+      for (int r = lane; r < tm.size; r += 32) s += buf[r * 8 + i];
+      s = warp_sum(s);
+      if (lane == 0) s_out[i] = s;
+    }
+  }
+  __syncthreads();
+  for (int i = 0; i < nv; ++i) v[i] = s_out[i];
+  __syncthreads();
+  tm.parity ^= 1;
+}
+
+// Multi-value all-reduce: every CTA has written nval partial doubles at
+// part[rank * nval ...] (in the current parity buffer); after the call out[k]
+// holds the fixed-order sum over CTAs, written by exactly one thread of the team.
+// The caller must team_sync before reading `out` from other CTAs.
+__device__ double* team_partials(Team& tm) { return tm.red + (long long)tm.parity * tm.red_stride; }
+
+__device__ void team_finish_multi(Team& tm, int nval, double* out, double scale) {
+  team_sync(tm);
+  double* buf = team_partials(tm);
+  for (int k = tm.gtid(); k < nval; k += tm.nthr()) {
+    double s = 0;
+    for (int r = 0; r < tm.size; ++r) s += buf[(long long)r * nval + k];
+    out[k] = s * scale;
+  }
+  tm.parity ^= 1;
+  team_sync(tm);
+}
+
+// ------------------------------------------------------------------ sum-of-products apply
+// Position decomposition of flat index idx along leg l.
+struct LegPos {
+  long long base;  // idx - i * stride
+  int i;
+};
+__device__ __forceinline__ LegPos leg_pos(const NodeDesc& nd, int l, long long idx) {
+  int st = nd.strides[l];
+  int i = (int)((idx / st) % nd.dims[l]);
+  return LegPos{idx - (long long)i * st, i};
+}
+
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t mode_dot(const double2* pool_unused, const double2* M, int D,
+                                                      int i, const double2* x, long long base, int stride) {
+  typename C2<T>::t acc;
+  acc.x = 0;
+  acc.y = 0;
+  const double2* row = M + (long long)i * D;
+  for (int k = 0; k < D; ++k) cmac<T>(acc, ld<T>(row + k), ld<T>(x + base + (long long)k * stride));
+  return acc;
+}
+
+// Stage 1: tmp[t] = first factor of two-factor term t applied to x
+template <typename T>
+__device__ void apply_stage1(const KernelParams& P, Team& tm, const NodeDesc& nd, const double2* x, const TermList& L,
+                             double2* tmp, long long tstride) {
+  const Term* terms = P.terms + L.first + (L.count - L.n2);
+  const long long N = nd.size;
+  for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+    for (int t = 0; t < L.n2; ++t) {
+      const Factor f = terms[t].f[0];
+      LegPos lp = leg_pos(nd, f.leg, idx);
+      auto a = mode_dot<T>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, x, lp.base, nd.strides[f.leg]);
+      tmp[t * tstride + idx] = make_double2((double)a.x, (double)a.y);
+    }
+  }
+}
+
+// Stage 2 value at idx: one-factor terms on x plus second factors on tmp
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t apply_stage2_at(const KernelParams& P, const NodeDesc& nd, const double2* x,
+                                                            const TermList& L, const double2* tmp, long long tstride,
+                                                            long long idx) {
+  typename C2<T>::t acc;
+  acc.x = 0;
+  acc.y = 0;
+  const Term* terms = P.terms + L.first;
+  const int n1 = L.count - L.n2;
+  for (int t = 0; t < n1; ++t) {
+    const Factor f = terms[t].f[0];
+    LegPos lp = leg_pos(nd, f.leg, idx);
+    auto a = mode_dot<T>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, x, lp.base, nd.strides[f.leg]);
+    acc.x += a.x;
+    acc.y += a.y;
+  }
+  for (int t = 0; t < L.n2; ++t) {
+    const Factor f = terms[n1 + t].f[1];
+    LegPos lp = leg_pos(nd, f.leg, idx);
+    auto a = mode_dot<T>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, tmp + t * tstride, lp.base, nd.strides[f.leg]);
+    acc.x += a.x;
+    acc.y += a.y;
+  }
+  return acc;
+}
+
+// ------------------------------------------------------------------ tridiagonal exponential
+// u = exp(-i s T) e_0 for the real symmetric tridiagonal T (diag a[0..m), off-diagonal
+// b[1..m) with b[k] coupling k-1 and k), by a Chebyshev expansion on the Gershgorin
+// interval: exp(-i z X) = J_0(z) + 2 sum_n (-i)^n J_n(z) T_n(X), X = (T - c)/R, z = s R.
+// Runs on one warp (lane k holds component k, m <= 32); FP64 throughout.
+__device__ void texp_warp(const double* a, const double* b, int m, double s, double* ure, double* uim) {
+  const int lane = threadIdx.x & 31;
+  const bool on = lane < m;
+  double ak = on ? a[lane] : 0.0;
+  double bk = (on && lane > 0) ? b[lane] : 0.0;
+  double bk1 = (lane + 1 < m) ? b[lane + 1] : 0.0;
+  double lo = on ? ak - fabs(bk) - fabs(bk1) : 1e300;
+  double hi = on ? ak + fabs(bk) + fabs(bk1) : -1e300;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  lo = __shfl_sync(0xffffffffu, lo, 0);
+  hi = __shfl_sync(0xffffffffu, hi, 0);
+  const double c = 0.5 * (hi + lo);
+  double R = 0.5 * (hi - lo);
+  double vre = (lane == 0) ? 1.0 : 0.0, vim = 0.0;  // current vector (complex)
+  if (R > 0.0) {
+    // sub-steps so that |z| <= 8 per Chebyshev expansion
+    double zt = fabs(s) * R;
+    if (!(zt < 1e4)) zt = 0.0;  // non-finite input: the caller reports it
+    int nsub = (int)ceil(zt / 8.0);
+    if (nsub < 1) nsub = 1;
+    const double z = s * R / nsub;     // signed
+    const double az = fabs(z);
+    int K = (int)ceil(1.2 * az + 18.0);
+    if (K > 64) K = 64;
+    // Bessel J_n(|z|) for n = lane and lane + 32 via the power series in Horner form
+    double J[2];
+    const double y = -0.25 * az * az;
+    for (int h = 0; h < 2; ++h) {
+      const int n = lane + 32 * h;
+      double acc = 1.0;
+      if (n < K) {
+        for (int j = 24; j >= 1; --j) acc = fma(acc * y, c_inv[j] * c_inv[j + n], 1.0);
+        J[h] = acc * pow(0.5 * az, (double)n) * c_invfact[n];
+      } else {
+        J[h] = 0.0;
+      }
+    }
+    const double dk = on ? (ak - c) / R : 0.0;
+    const double ek = on ? bk / R : 0.0;
+    const double fk = on ? bk1 / R : 0.0;
+    for (int sub = 0; sub < nsub; ++sub) {
+      // Chebyshev on the complex vector v: w = sum_n coef_n T_n(X) v with real T_n
+      double t0r = vre, t0i = vim;
+      double accr = 0.0, acci = 0.0;
+      double tmr = 0.0, tmi = 0.0;   // T_{n-1} v
+      double tr = t0r, ti = t0i;     // T_n v
+      for (int n = 0; n < K; ++n) {
+        const double Jn = __shfl_sync(0xffffffffu, J[n >> 5], n & 31);
+        double cr, ci;  // coef_n = (n ? 2 : 1) (-i sgn(z))^n J_n(|z|)
+        const double w = (n ? 2.0 : 1.0) * Jn;
+        const int q = n & 3;
+        const bool neg = z < 0.0;
+        // (-i)^n for z > 0; (+i)^n for z < 0
+        if (q == 0) { cr = w; ci = 0.0; }
+        else if (q == 2) { cr = -w; ci = 0.0; }
+        else if ((q == 1) != neg) { cr = 0.0; ci = -w; }
+        else { cr = 0.0; ci = w; }
+        accr = fma(cr, tr, fma(-ci, ti, accr));
+        acci = fma(cr, ti, fma(ci, tr, acci));
+        // next Chebyshev vector
+        double trl = __shfl_up_sync(0xffffffffu, tr, 1), til = __shfl_up_sync(0xffffffffu, ti, 1);
+        double trr = __shfl_down_sync(0xffffffffu, tr, 1), tir = __shfl_down_sync(0xffffffffu, ti, 1);
+        if (lane == 0) { trl = 0.0; til = 0.0; }
+        if (lane + 1 >= m) { trr = 0.0; tir = 0.0; }
+        double xr = fma(dk, tr, fma(ek, trl, fk * trr));
+        double xi = fma(dk, ti, fma(ek, til, fk * tir));
+        double nr, ni;
+        if (n == 0) { nr = xr; ni = xi; }
+        else { nr = fma(2.0, xr, -tmr); ni = fma(2.0, xi, -tmi); }
+        if (!on) { nr = 0.0; ni = 0.0; }
+        tmr = tr; tmi = ti;
+        tr = nr; ti = ni;
+      }
+      vre = accr;
+      vim = acci;
+    }
+  }
+  // global phase exp(-i s c)
+  double sn, cs;
+  sincos(-s * c, &sn, &cs);
+  const double rr = vre * cs - vim * sn;
+  const double ri = vre * sn + vim * cs;
+  if (on) { ure[lane] = rr; uim[lane] = ri; }
+}
+
+// ------------------------------------------------------------------ Lanczos exponential
+struct KrylovShared {
+  double alpha[TTNS_KMAX + 1];
+  double beta[TTNS_KMAX + 2];   // beta[j] couples j-1 and j
+  double scale[TTNS_KMAX + 1];  // q_j = scale[j] * K_j
+  double ure[TTNS_KMAX];
+  double uim[TTNS_KMAX];
+  int flag;
+};
+
+template <typename T>
+__device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2* work, double tau) {
+  __shared__ KrylovShared ks;
+  const NodeDesc nd = P.nodes[I.node];
+  const TermList L = P.lists[I.terms];
+  const long long N = nd.size;
+  const long long kv = P.kvec;
+  double2* x = P.pool + nd.off;
+  double2* Kb = work;                           // K_1..K_mmax at Kb + (j-1)*kv
+  double2* tmp = work + (long long)P.mmax * kv;  // n_tmp temporaries
+  const double s = I.sign * tau / HBAR_EVFS;     // exp(-i s H)
+  auto Kp = [&](int j) -> double2* { return j == 0 ? x : Kb + (long long)(j - 1) * kv; };
+
+  double v[2];
+  v[0] = 0;
+  for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+    double2 a = x[idx];
+    v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
+  }
+  team_allreduce(tm, v, 1);
+  const double beta0 = sqrt(v[0]);
+  if (!(beta0 > 0.0)) {
+    if (!(beta0 == 0.0)) set_status(P.ctl, ST_NONFINITE, OP_FWD, I.node);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    ks.scale[0] = 1.0 / beta0;
+    ks.beta[0] = 0.0;
+  }
+  __syncthreads();
+  int hint = P.mhist[I.hist];
+  if (hint < 2) hint = 2;
+  const int mmax = min(P.mmax, (int)(N < (long long)TTNS_KMAX ? N : (long long)TTNS_KMAX));
+  int m = 0;
+  bool conv = false;
+  for (int j = 0; j < mmax; ++j) {
+    double2* Kj = Kp(j);
+    double2* Kjm = j > 0 ? Kp(j - 1) : x;
+    double2* W = Kb + (long long)j * kv;  // slot of K_{j+1}
+    const double sj = ks.scale[j];
+    const double bj = ks.beta[j];
+    const double sjm = j > 0 ? ks.scale[j - 1] : 0.0;
+    if (L.n2 > 0) {
+      apply_stage1<T>(P, tm, nd, Kj, L, tmp, kv);
+      team_sync(tm);
+    }
+    double part[1] = {0.0};
+    for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+      auto a = apply_stage2_at<T>(P, nd, Kj, L, tmp, kv, idx);
+      double2 kj = Kj[idx];
+      double wr = sj * (double)a.x, wi = sj * (double)a.y;
+      if (j > 0) {
+        double2 km = Kjm[idx];
+        wr = fma(-bj * sjm, km.x, wr);
+        wi = fma(-bj * sjm, km.y, wi);
+      }
+      W[idx] = make_double2(wr, wi);
+      part[0] = fma(kj.x, wr, fma(kj.y, wi, part[0]));  // Re(conj(K_j) w)
+    }
+    team_allreduce(tm, part, 1);
+    const double aj = part[0] * sj;
+    part[0] = 0.0;
+    for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+      double2 kj = Kj[idx];
+      double2 w = W[idx];
+      w.x = fma(-aj * sj, kj.x, w.x);
+      w.y = fma(-aj * sj, kj.y, w.y);
+      W[idx] = w;
+      part[0] = fma(w.x, w.x, fma(w.y, w.y, part[0]));
+    }
+    team_allreduce(tm, part, 1);
+    const double bnext = sqrt(part[0]);
+    if (threadIdx.x == 0) {
+      ks.alpha[j] = aj;
+      ks.beta[j + 1] = bnext;
+      ks.scale[j + 1] = bnext > 0.0 ? 1.0 / bnext : 0.0;
+    }
+    __syncthreads();
+    m = j + 1;
+    if (m >= hint - 1 || m == mmax || !(bnext > 0.0)) {
+      if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s, ks.ure, ks.uim);
+      __syncthreads();
+      const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);
+      const double err = bnext * um;
+      if (!(err == err)) {
+        set_status(P.ctl, ST_NONFINITE, I.op, I.node);
+        conv = true;
+      } else if (err <= P.tol || !(bnext > 0.0)) {
+        conv = true;
+      }
+      if (conv || m == mmax) break;
+    }
+  }
+  if (!conv && tm.rank == 0 && threadIdx.x == 0) atomicAdd(&P.ctl->not_converged, 1ull);
+  // y = beta0 * sum_k u_k q_k written over x (each thread reads its own K_0 = x entries first)
+  for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+    double yr = 0.0, yi = 0.0;
+    for (int k = 0; k < m; ++k) {
+      double2 q = Kp(k)[idx];
+      const double sc = beta0 * ks.scale[k];
+      const double cr = ks.ure[k] * sc, ci = ks.uim[k] * sc;
+      yr = fma(cr, q.x, fma(-ci, q.y, yr));
+      yi = fma(cr, q.y, fma(ci, q.x, yi));
+    }
+    x[idx] = make_double2(yr, yi);
+  }
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    P.mhist[I.hist] = m;
+    atomicAdd(&P.ctl->krylov_iters, (unsigned long long)m);
+    atomicAdd(&P.ctl->applies, (unsigned long long)m);
+    atomicAdd(&P.ctl->flops, I.flops * m);
+  }
+  team_sync(tm);
+}
+
+// ------------------------------------------------------------------ Householder QR
+// A_v (matricised: rows = all other legs in order, columns = leg I.leg) = Q R with the
+// completion rule of the oracle: null sub-columns (norm <= 1e-8 ||M||_F) get the identity
+// reflector and R_jj = 0; Q = H_0 ... H_{n-1} I[:, :n] through the compact WY form
+// Q = I - V T V^H; finally R_jj is made real and >= 0.  FP64.
+struct QRShared {
+  double tau[TTNS_MAX_D];
+  double2 vhead[TTNS_MAX_D];
+  double2 rdiag[TTNS_MAX_D];
+  double2 coef[TTNS_MAX_D];
+  double2 ph[TTNS_MAX_D];
+};
+
+__device__ __forceinline__ long long qr_addr(const NodeDesc& nd, int l, long long r, int c) {
+  const long long st = nd.strides[l];
+  const long long p = r / st, q = r - p * st;
+  return p * nd.dims[l] * st + (long long)c * st + q;
+}
+
+// Rows owned by a CTA of the team: r = rank*NT + t + k*nthr, t in [0, NT).
+// The helpers below walk them in a fixed order.
+__device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
+  __shared__ QRShared qs;
+  const NodeDesc nd = P.nodes[I.node];
+  const int l = I.leg;
+  const int n = nd.dims[l];
+  const long long rows = nd.size / n;
+  double2* A = P.pool + nd.off;
+  double2* W = work;  // column-major: W[c * rows + r]
+  double2* Rout = P.pool + P.trees[I.tree].bond_off;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // per-CTA scratch for the small matrices G (Gram of V), T, Z
+  double2* G = P.cta_scratch + (long long)blockIdx.x * P.cta_scratch_stride;
+  double2* Tm = G + TTNS_MAX_D * TTNS_MAX_D;
+  double2* Z = Tm + TTNS_MAX_D * TTNS_MAX_D;
+  // copy and column-0 reduction: {fro^2, sigma_0^2, x0.re, x0.im}
+  double v[4] = {0, 0, 0, 0};
+  for (long long r = tm.gtid(); r < rows; r += tm.nthr()) {
+    for (int c = 0; c < n; ++c) {
+      double2 a = A[qr_addr(nd, l, r, c)];
+      W[(long long)c * rows + r] = a;
+      v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
+      if (c == 0) {
+        v[1] = fma(a.x, a.x, fma(a.y, a.y, v[1]));
+        if (r == 0) { v[2] = a.x; v[3] = a.y; }
+      }
+    }
+  }
+  team_allreduce(tm, v, 4);
+  const double thr = QR_NULL_REL * sqrt(v[0]);
+  double sig2 = v[1];
+  double2 x0 = make_double2(v[2], v[3]);
+  const long long r_cta0 = (long long)tm.rank * NT;
+  const long long r_step = (long long)tm.nthr();
+  for (int j = 0; j < n; ++j) {
+    const double sigma = sqrt(sig2);
+    double tau = 0.0;
+    double2 vh = make_double2(0, 0), alpha = make_double2(0, 0);
+    const bool null = !(sigma > thr);
+    if (!null) {
+      const double ax = sqrt(x0.x * x0.x + x0.y * x0.y);
+      double2 ph = ax > 0.0 ? make_double2(x0.x / ax, x0.y / ax) : make_double2(1.0, 0.0);
+      alpha = make_double2(-ph.x * sigma, -ph.y * sigma);
+      vh = make_double2(x0.x - alpha.x, x0.y - alpha.y);
+      const double vn2 = sig2 - ax * ax + (vh.x * vh.x + vh.y * vh.y);
+      tau = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+    }
+    if (threadIdx.x == 0) {
+      qs.tau[j] = tau;
+      qs.vhead[j] = vh;
+      qs.rdiag[j] = alpha;
+    }
+    const int nk = n - j - 1;
+    if (!null && nk > 0) {
+      // reduction B: c_k = tau sum_{r >= j} conj(v_r) W[k][r], k > j.  Warp w handles
+      // columns k = w, w + NWARP, ...; its lanes walk the CTA's rows.
+      double* part = team_partials(tm);
+      for (int k = warp; k < nk; k += NWARP) {
+        const double2* Wk = W + (long long)(j + 1 + k) * rows;
+        double ar = 0, ai = 0;
+        for (long long rb = r_cta0; rb < rows; rb += r_step) {
+          for (int t = lane; t < NT; t += 32) {
+            const long long r = rb + t;
+            if (r >= rows || r < j) continue;
+            const double2 vr = (r == j) ? vh : W[(long long)j * rows + r];
+            const double2 w = Wk[r];
+            ar = fma(vr.x, w.x, fma(vr.y, w.y, ar));
+            ai = fma(vr.x, w.y, fma(-vr.y, w.x, ai));
+          }
+        }
+        ar = warp_sum(ar);
+        ai = warp_sum(ai);
+        if (lane == 0) {
+          part[(long long)tm.rank * 2 * nk + 2 * k] = ar;
+          part[(long long)tm.rank * 2 * nk + 2 * k + 1] = ai;
+        }
+      }
+      __syncthreads();
+      team_sync(tm);
+      for (int k = threadIdx.x; k < 2 * nk; k += NT) {
+        double a = 0;
+        for (int r = 0; r < tm.size; ++r) a += part[(long long)r * 2 * nk + k];
+        if (k & 1) qs.coef[k >> 1].y = a * tau; else qs.coef[k >> 1].x = a * tau;
+      }
+      tm.parity ^= 1;
+      __syncthreads();
+      // update trailing columns and gather the next column's reduction
+      double nv[3] = {0, 0, 0};
+      for (long long r = tm.gtid(); r < rows; r += tm.nthr()) {
+        if (r < j) continue;
+        const double2 vr = (r == j) ? vh : W[(long long)j * rows + r];
+        for (int k = 0; k < nk; ++k) {
+          const double2 ck = qs.coef[k];
+          double2* wp = &W[(long long)(j + 1 + k) * rows + r];
+          double2 w = *wp;
+          w.x -= vr.x * ck.x - vr.y * ck.y;
+          w.y -= vr.x * ck.y + vr.y * ck.x;
+          *wp = w;
+          if (k == 0 && r >= j + 1) {
+            nv[0] = fma(w.x, w.x, fma(w.y, w.y, nv[0]));
+            if (r == j + 1) { nv[1] = w.x; nv[2] = w.y; }
+          }
+        }
+      }
+      team_allreduce(tm, nv, 3);
+      sig2 = nv[0];
+      x0 = make_double2(nv[1], nv[2]);
+    } else if (nk > 0) {
+      // no reflection: the next column's reduction on unchanged data
+      double nv[3] = {0, 0, 0};
+      for (long long r = tm.gtid(); r < rows; r += tm.nthr()) {
+        if (r < j + 1) continue;
+        const double2 w = W[(long long)(j + 1) * rows + r];
+        nv[0] = fma(w.x, w.x, fma(w.y, w.y, nv[0]));
+        if (r == j + 1) { nv[1] = w.x; nv[2] = w.y; }
+      }
+      team_allreduce(tm, nv, 3);
+      sig2 = nv[0];
+      x0 = make_double2(nv[1], nv[2]);
+    }
+  }
+  __syncthreads();
+  // Gram of the Householder vectors: G[a][b] = v_a^H v_b over rows r >= max(a, b)
+  {
+    double* part = team_partials(tm);
+    const int n2 = n * n;
+    for (int pidx = threadIdx.x; pidx < n2; pidx += NT) {
+      const int a = pidx / n, b = pidx % n;
+      double gr = 0, gi = 0;
+      if (a <= b && qs.tau[a] != 0.0 && qs.tau[b] != 0.0) {
+        for (long long rb = r_cta0; rb < rows; rb += r_step) {
+          const long long rend = min(rb + NT, rows);
+          for (long long r = max(rb, (long long)b); r < rend; ++r) {
+            const double2 va = (r == a) ? qs.vhead[a] : W[(long long)a * rows + r];
+            const double2 vb = (r == b) ? qs.vhead[b] : W[(long long)b * rows + r];
+            gr = fma(va.x, vb.x, fma(va.y, vb.y, gr));
+            gi = fma(va.x, vb.y, fma(-va.y, vb.x, gi));
+          }
+        }
+      }
+      part[(long long)tm.rank * 2 * n2 + 2 * pidx] = gr;
+      part[(long long)tm.rank * 2 * n2 + 2 * pidx + 1] = gi;
+    }
+    __syncthreads();
+    team_sync(tm);
+    for (int pidx = threadIdx.x; pidx < n2; pidx += NT) {
+      const int a = pidx / n, b = pidx % n;
+      if (a > b) continue;
+      double gr = 0, gi = 0;
+      for (int r = 0; r < tm.size; ++r) {
+        gr += part[(long long)r * 2 * n2 + 2 * pidx];
+        gi += part[(long long)r * 2 * n2 + 2 * pidx + 1];
+      }
+      G[a * TTNS_MAX_D + b] = make_double2(gr, gi);
+      G[b * TTNS_MAX_D + a] = make_double2(gr, -gi);
+    }
+    tm.parity ^= 1;
+    __syncthreads();
+  }
+  // T (upper triangular): T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j]
+  for (int idx = threadIdx.x; idx < n * n; idx += NT) Tm[idx / n * TTNS_MAX_D + idx % n] = make_double2(0, 0);
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    const double tj = qs.tau[j];
+    if (threadIdx.x < j && tj != 0.0) {
+      const int i = threadIdx.x;
+      double sr = 0, si = 0;
+      for (int k = i; k < j; ++k) {
+        const double2 t = Tm[i * TTNS_MAX_D + k];
+        const double2 g = G[k * TTNS_MAX_D + j];
+        sr += t.x * g.x - t.y * g.y;
+        si += t.x * g.y + t.y * g.x;
+      }
+      Tm[i * TTNS_MAX_D + j] = make_double2(-tj * sr, -tj * si);
+    }
+    if (threadIdx.x == 0) Tm[j * TTNS_MAX_D + j] = make_double2(tj, 0.0);
+    __syncthreads();
+  }
+  // Z = T V_top^H: Z[j][c] = sum_{j <= i <= c} T[j][i] conj(V[c][i])
+  for (int idx = threadIdx.x; idx < n * n; idx += NT) {
+    const int j = idx / n, c = idx % n;
+    double zr = 0, zi = 0;
+    for (int i = j; i <= c; ++i) {
+      if (qs.tau[i] == 0.0) continue;
+      const double2 t = Tm[j * TTNS_MAX_D + i];
+      const double2 vci = (c == i) ? qs.vhead[i] : W[(long long)i * rows + c];
+      zr += t.x * vci.x + t.y * vci.y;
+      zi += t.y * vci.x - t.x * vci.y;
+    }
+    Z[j * TTNS_MAX_D + c] = make_double2(zr, zi);
+  }
+  // phases of the diagonal of R
+  for (int j = threadIdx.x; j < n; j += NT) {
+    const double2 a = qs.rdiag[j];
+    const double aa = sqrt(a.x * a.x + a.y * a.y);
+    qs.ph[j] = aa > 0.0 ? make_double2(a.x / aa, a.y / aa) : make_double2(1.0, 0.0);
+  }
+  __syncthreads();
+  // R (row j scaled by conj(ph_j)) into the bond buffer: R[j][k] = W[k][j] (k > j), diag alpha_j
+  if (tm.rank == 0) {
+    for (int idx = threadIdx.x; idx < n * n; idx += NT) {
+      const int j = idx / n, k = idx % n;
+      double2 r = make_double2(0, 0);
+      if (k > j) r = W[(long long)k * rows + j];
+      else if (k == j) r = qs.rdiag[j];
+      const double2 p = qs.ph[j];
+      Rout[idx] = make_double2(r.x * p.x + r.y * p.y, r.y * p.x - r.x * p.y);
+    }
+  }
+  // Q[r][c] = (delta_rc - sum_j V[r][j] Z[j][c]) * ph_c, written back into the tensor
+  for (long long r = tm.gtid(); r < rows; r += tm.nthr()) {
+    const int jmax = (int)(r < (long long)n - 1 ? r : (long long)n - 1);
+    for (int c = 0; c < n; ++c) {
+      double qre = (r == c) ? 1.0 : 0.0, qim = 0.0;
+      for (int j = 0; j <= jmax; ++j) {
+        if (qs.tau[j] == 0.0) continue;
+        const double2 vr = (r == j) ? qs.vhead[j] : W[(long long)j * rows + r];
+        const double2 z = Z[j * TTNS_MAX_D + c];
+        qre -= vr.x * z.x - vr.y * z.y;
+        qim -= vr.x * z.y + vr.y * z.x;
+      }
+      const double2 p = qs.ph[c];
+      A[qr_addr(nd, l, r, c)] = make_double2(qre * p.x - qim * p.y, qre * p.y + qim * p.x);
+    }
+  }
+  team_sync(tm);
+}
+
+// ------------------------------------------------------------------ absorb
+// A_u <- R applied on leg I.leg (FP64), through a temporary
+__device__ void op_absorb(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
+  const NodeDesc nd = P.nodes[I.node];
+  const long long N = nd.size;
+  double2* A = P.pool + nd.off;
+  const double2* R = P.pool + P.trees[I.tree].bond_off;
+  const int l = I.leg;
+  for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+    LegPos lp = leg_pos(nd, l, idx);
+    auto a = mode_dot<double>(P.pool, R, nd.dims[l], lp.i, A, lp.base, nd.strides[l]);
+    work[idx] = a;
+  }
+  team_sync(tm);
+  for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) A[idx] = work[idx];
+  team_sync(tm);
+}
+
+// ------------------------------------------------------------------ environment update
+// env(u -> v): block 0 = Q^H (H-terms of u without v) Q, block 1+b = Q^H (channel factor b) Q,
+// contracted over every leg of Q except the leg toward v.
+template <typename T>
+__device__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
+  const NodeDesc nd = P.nodes[I.node];
+  const TermList L = P.lists[I.terms];
+  const long long N = nd.size;
+  const long long kv = P.kvec;
+  const double2* Q = P.pool + nd.off;
+  double2* tmp = work + (long long)P.mmax * kv;
+  double2* Y = work;  // Y_0 .. Y_nchan at work + b*kv (fits: 1 + nchan <= mmax)
+  const int l = I.leg;
+  const int D = I.D;
+  const int nb = 1 + I.nchan;
+  if (L.n2 > 0) {
+    apply_stage1<T>(P, tm, nd, Q, L, tmp, kv);
+    team_sync(tm);
+  }
+  for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+    auto a = apply_stage2_at<T>(P, nd, Q, L, tmp, kv, idx);
+    Y[idx] = make_double2((double)a.x, (double)a.y);
+    for (int b = 0; b < I.nchan; ++b) {
+      const Factor f = P.chans[I.chan_first + b];
+      LegPos lp = leg_pos(nd, f.leg, idx);
+      auto c = mode_dot<T>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, Q, lp.base, nd.strides[f.leg]);
+      Y[(long long)(1 + b) * kv + idx] = make_double2((double)c.x, (double)c.y);
+    }
+  }
+  team_sync(tm);
+  // projection: out[b][a][a'] = sum_rows conj(Q[row, a]) Y_b[row, a']
+  const long long rows = N / D;
+  const int nval = nb * D * D;
+  double* part = team_partials(tm);
+  const long long st = nd.strides[l];
+  // rows split across CTAs in contiguous chunks; each thread owns output values
+  const long long chunk = (rows + tm.size - 1) / tm.size;
+  const long long r_begin = (long long)tm.rank * chunk;
+  const long long r_end = min(rows, r_begin + chunk);
+  for (int o = threadIdx.x; o < nval; o += NT) {
+    const int b = o / (D * D);
+    const int a = (o / D) % D;
+    const int a2 = o % D;
+    const double2* Yb = Y + (long long)b * kv;
+    double accr = 0, acci = 0;
+    for (long long r0 = r_begin; r0 < r_end; r0 += 64) {
+      typename C2<T>::t s;
+      s.x = 0;
+      s.y = 0;
+      const long long r1 = min(r_end, r0 + 64);
+      for (long long r = r0; r < r1; ++r) {
+        const long long p = r / st, q = r - p * st;
+        const long long base = p * D * st + q;
+        auto qa = ld<T>(Q + base + (long long)a * st);
+        auto y = ld<T>(Yb + base + (long long)a2 * st);
+        s.x = fma(qa.x, y.x, fma(qa.y, y.y, s.x));
+        s.y = fma(qa.x, y.y, fma(-qa.y, y.x, s.y));
+      }
+      accr += (double)s.x;
+      acci += (double)s.y;
+    }
+    part[(long long)tm.rank * 2 * nval + 2 * o] = accr;
+    part[(long long)tm.rank * 2 * nval + 2 * o + 1] = acci;
+  }
+  team_finish_multi(tm, 2 * nval, (double*)(P.pool + I.env_out), 1.0);
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    atomicAdd(&P.ctl->applies, 1ull);
+    atomicAdd(&P.ctl->flops, I.flops);
+  }
+}
+
+// ------------------------------------------------------------------ record rho_S
+__device__ void op_record(const KernelParams& P, Team& tm, const Instr& I, int* counter) {
+  const TreeDesc td = P.trees[I.tree];
+  if (td.traj_off < 0) return;
+  const NodeDesc nd = P.nodes[td.node0];
+  const int ne = td.n_el;
+  const long long rows = nd.size / ne;  // phys leg is the last leg: stride 1
+  const double2* A = P.pool + nd.off;
+  const int nval = ne * ne;
+  double* part = team_partials(tm);
+  const long long chunk = (rows + tm.size - 1) / tm.size;
+  const long long r_begin = (long long)tm.rank * chunk, r_end = min(rows, r_begin + chunk);
+  for (int o = threadIdx.x; o < nval; o += NT) {
+    const int s1 = o / ne, s2 = o % ne;
+    double accr = 0, acci = 0;
+    for (long long r = r_begin; r < r_end; ++r) {
+      double2 a = A[r * ne + s1], b = A[r * ne + s2];
+      accr = fma(a.x, b.x, fma(a.y, b.y, accr));
+      acci = fma(a.y, b.x, fma(-a.x, b.y, acci));
+    }
+    part[(long long)tm.rank * 2 * nval + 2 * o] = accr;
+    part[(long long)tm.rank * 2 * nval + 2 * o + 1] = acci;
+  }
+  int slot = *counter;
+  if (slot >= P.max_record) slot = P.max_record - 1;
+  team_finish_multi(tm, 2 * nval, (double*)(P.pool + td.traj_off + (long long)slot * nval), 1.0);
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    *counter = *counter + 1;
+    atomicAdd(&P.ctl->steps, 1ull);
+  }
+}
+
+// ------------------------------------------------------------------ interpreter
+template <typename T>
+__device__ void exec(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
+  const double tau = 0.5 * P.dt;
+  switch (I.op) {
+    case OP_FWD:
+    case OP_BOND:
+      op_expm<T>(P, tm, I, work, tau);
+      break;
+    case OP_QR:
+      op_qr(P, tm, I, work);
+      break;
+    case OP_ENV:
+      op_env<T>(P, tm, I, work);
+      break;
+    case OP_ABSORB:
+      op_absorb(P, tm, I, work);
+      break;
+    case OP_RECORD:
+      op_record(P, tm, I, P.traj_count + I.tree);
+      break;
+  }
+}
+
+template <typename T>
+__device__ void run(const KernelParams& P, int phase) {
+  const int cs = P.cluster_ctas;
+  const int cluster_id = blockIdx.x / cs;
+  const int n_clusters = gridDim.x / cs;
+  const int crank = (int)cg::this_cluster().block_rank();
+  Team ct;
+  ct.kind = TEAM_CLUSTER;
+  ct.rank = crank;
+  ct.size = cs;
+  ct.red = P.red + (long long)cluster_id * 2 * P.red_stride;
+  ct.red_stride = P.red_stride;
+  ct.parity = 0;
+  ct.ctl = P.ctl;
+  ct.spin_limit = P.spin_limit;
+  double2* cwork = P.work + (long long)cluster_id * P.work_stride;
+  if (P.batched) {
+    for (int tree = cluster_id; tree < P.n_trees; tree += n_clusters) {
+      const TreeDesc& td = P.trees[tree];
+      const int first = phase == 0 ? td.init_first : td.prog_first;
+      const int count = phase == 0 ? td.init_count : td.prog_count;
+      const int nst = phase == 0 ? 1 : P.n_steps;
+      for (int s = 0; s < nst; ++s) {
+        for (int k = 0; k < count; ++k) {
+          exec<T>(P, ct, P.prog[first + k], cwork);
+        }
+      }
+    }
+    return;
+  }
+  Team gt;
+  gt.kind = TEAM_GRID;
+  gt.rank = blockIdx.x;
+  gt.size = gridDim.x;
+  gt.red = P.red_grid;
+  gt.red_stride = P.red_stride_grid;
+  gt.parity = 0;
+  gt.ctl = P.ctl;
+  gt.spin_limit = P.spin_limit;
+  const TreeDesc& td = P.trees[0];
+  const int first = phase == 0 ? td.init_first : td.prog_first;
+  const int count = phase == 0 ? td.init_count : td.prog_count;
+  const int nst = phase == 0 ? 1 : P.n_steps;
+  int prev = TEAM_GRID;
+  for (int s = 0; s < nst; ++s) {
+    for (int k = 0; k < count; ++k) {
+      const Instr& I = P.prog[first + k];
+      if (I.team == TEAM_GRID) {
+        if (prev == TEAM_CLUSTER) grid_sync(P.ctl, P.spin_limit);
+        exec<T>(P, gt, I, P.work);
+      } else if (cluster_id == 0) {
+        exec<T>(P, ct, I, cwork);
+      }
+      prev = I.team;
+    }
+  }
+  if (prev == TEAM_CLUSTER) grid_sync(P.ctl, P.spin_limit);
+}
+
+__global__ void __launch_bounds__(NT, 1) k_sweep(KernelParams P, int phase) {
+  if (P.precision == 0)
+    run<double>(P, phase);
+  else
+    run<float>(P, phase);
+}
+
+// ------------------------------------------------------------------ observables
+// Bond or site density of node v's leg l from the incoming parent-bond density rho_in
+// (D_p x D_p, or nullptr at the root):
+//   out[b][b'] = sum rho_in[p', p] A[p, .., b, ..] conj(A[p', .., b', ..]) over the other legs.
+// One CTA per call (small sizes), except that the root (rho_in == nullptr) may be large:
+// a grid of CTAs writes partials, reduced by k_reduce_partials.
+__global__ void k_density_partial(const double2* pool, NodeDesc nd, int l, const double2* rho_in, double* partials) {
+  const int D = nd.dims[l];
+  const long long N = nd.size;
+  const long long st = nd.strides[l];
+  const long long rows = N / D;
+  const long long chunk = (rows + gridDim.x - 1) / gridDim.x;
+  const long long r_begin = (long long)blockIdx.x * chunk, r_end = min(rows, r_begin + chunk);
+  const double2* A = pool + nd.off;
+  const int Dp = rho_in ? nd.dims[0] : 0;
+  const long long stp = nd.strides[0];
+  for (int o = threadIdx.x; o < D * D; o += blockDim.x) {
+    const int b = o / D, b2 = o % D;
+    double accr = 0, acci = 0;
+    for (long long r = r_begin; r < r_end; ++r) {
+      const long long p = r / st, q = r - p * st;
+      const long long base = p * D * st + q;
+      const double2 y = A[base + (long long)b2 * st];
+      double2 xa;
+      if (!rho_in) {
+        xa = A[base + (long long)b * st];
+      } else {
+        // X[idx] = sum_a' rho_in[a'][a] A[a', ...] evaluated at idx = base + b*st (a = parent index)
+        const long long idx = base + (long long)b * st;
+        const int a = (int)((idx / stp) % Dp);
+        const long long b0 = idx - (long long)a * stp;
+        xa = make_double2(0, 0);
+        for (int a2 = 0; a2 < Dp; ++a2) {
+          const double2 r_ = rho_in[a2 * Dp + a];
+          const double2 v = A[b0 + (long long)a2 * stp];
+          xa.x += r_.x * v.x - r_.y * v.y;
+          xa.y += r_.x * v.y + r_.y * v.x;
+        }
+      }
+      accr = fma(xa.x, y.x, fma(xa.y, y.y, accr));
+      acci = fma(xa.y, y.x, fma(-xa.x, y.y, acci));
+    }
+    partials[(long long)blockIdx.x * 2 * D * D + 2 * o] = accr;
+    partials[(long long)blockIdx.x * 2 * D * D + 2 * o + 1] = acci;
+  }
+}
+
+__global__ void k_reduce_partials(const double* partials, int nblocks, int nval, double* out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nval; k += gridDim.x * blockDim.x) {
+    double s = 0;
+    for (int b = 0; b < nblocks; ++b) s += partials[(long long)b * nval + k];
+    out[k] = s;
+  }
+}
+
+// <n> = sum_s s Re(rho[s][s]) of one site density
+__global__ void k_occ(const double2* dens, int d, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double o = 0;
+    for (int q = 1; q < d; ++q) o += q * dens[q * d + q].x;
+    *out = o;
+  }
+}
+
+// norm^2 and <A|H_eff|A> at the root with FP64 terms
+__global__ void k_energy_partial(KernelParams P, int node, int terms, double* partials) {
+  const NodeDesc nd = P.nodes[node];
+  const TermList L = P.lists[terms];
+  const double2* x = P.pool + nd.off;
+  const long long N = nd.size;
+  double e = 0, nn = 0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (long long)gridDim.x * blockDim.x) {
+    auto a = apply_stage2_at<double>(P, nd, x, L, P.work + (long long)P.mmax * P.kvec, P.kvec, idx);
+    double2 v = x[idx];
+    e = fma(v.x, a.x, fma(v.y, a.y, e));
+    nn = fma(v.x, v.x, fma(v.y, v.y, nn));
+  }
+  __shared__ double s1[NWARP], s2[NWARP];
+  e = warp_sum(e);
+  nn = warp_sum(nn);
+  if ((threadIdx.x & 31) == 0) { s1[threadIdx.x >> 5] = e; s2[threadIdx.x >> 5] = nn; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < NWARP; ++w) { a += s1[w]; b += s2[w]; }
+    partials[2 * blockIdx.x] = a;
+    partials[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// stage 1 of a term list over a whole tensor, written to the worker-0 temporaries
+__global__ void k_stage1(KernelParams P, int node, int terms) {
+  const NodeDesc nd = P.nodes[node];
+  const TermList L = P.lists[terms];
+  const Term* tl = P.terms + L.first + (L.count - L.n2);
+  const double2* x = P.pool + nd.off;
+  double2* tmp = P.work + (long long)P.mmax * P.kvec;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nd.size; idx += (long long)gridDim.x * blockDim.x) {
+    for (int t = 0; t < L.n2; ++t) {
+      const Factor f = tl[t].f[0];
+      LegPos lp = leg_pos(nd, f.leg, idx);
+      auto a = mode_dot<double>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, x, lp.base, nd.strides[f.leg]);
+      tmp[t * P.kvec + idx] = a;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host launch helpers
+static bool g_tables_set = false;
+
+cudaError_t upload_constants() {
+  if (g_tables_set) return cudaSuccess;
+  double inv[256], invf[128];
+  inv[0] = 0.0;
+  for (int k = 1; k < 256; ++k) inv[k] = 1.0 / k;
+  invf[0] = 1.0;
+  for (int k = 1; k < 128; ++k) invf[k] = invf[k - 1] / k;
+  cudaError_t e = cudaMemcpyToSymbol(c_inv, inv, sizeof(inv));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_invfact, invf, sizeof(invf));
+  if (e == cudaSuccess) g_tables_set = true;
+  return e;
+}
+
+cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster, cudaStream_t stream) {
+  cudaError_t e = upload_constants();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeCooperative;
+  at[1].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_sweep, P, phase);
+}
+
+cudaError_t max_grid_for(int cluster, int* grid) {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(NT);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&nclusters, k_sweep, &cfg);
+  if (e != cudaSuccess) return e;
+  *grid = nclusters * cluster;
+  return cudaSuccess;
+}
+
+cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double* partials,
+                           int nblocks, double* out, cudaStream_t st) {
+  k_density_partial<<<nblocks, NT, 0, st>>>(pool, nd, l, rho_in, partials);
+  const int D = nd.dims[l];
+  k_reduce_partials<<<(2 * D * D + NT - 1) / NT, NT, 0, st>>>(partials, nblocks, 2 * D * D, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_occ(const double2* dens, int d, double* out, cudaStream_t st) {
+  k_occ<<<1, 32, 0, st>>>(dens, d, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const KernelParams& P, int node, int terms, int n2, double* partials, int nblocks,
+                          double* out, cudaStream_t st) {
+  if (n2 > 0) k_stage1<<<nblocks, NT, 0, st>>>(P, node, terms);
+  k_energy_partial<<<nblocks, NT, 0, st>>>(P, node, terms, partials);
+  k_reduce_partials<<<1, NT, 0, st>>>(partials, nblocks, 2, out);
+  return cudaGetLastError();
+}
+
+}  // namespace ttns

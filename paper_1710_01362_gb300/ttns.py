@@ -1,0 +1,303 @@
+"""Thin ctypes binding of libttns.so (argument marshalling only).
+
+Every call maps one-to-one onto an entry point of include/ttns.h.  The library
+must be built (``paper_1710_01362_gb300.build.build()``); importing this module
+without it raises, and there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libttns.so")
+
+TTNS_FP64 = 0
+TTNS_MIXED = 1
+
+STATUS = {0: "ok", 1: "invalid", 2: "oom", 3: "cuda", 4: "not converged", 5: "timeout", 6: "nonfinite", 7: "io"}
+
+EXPORTS = [
+    "ttns_build_tree", "ttns_build_batch", "ttns_step", "ttns_sync", "ttns_reduced_density_matrix",
+    "ttns_occupations", "ttns_observables", "ttns_trajectory", "ttns_populations_device", "ttns_get_counters",
+    "ttns_node_info", "ttns_get_node", "ttns_save", "ttns_load_state", "ttns_last_error", "ttns_free",
+    "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan",
+]
+
+
+class TTNSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int), ("krylov_tol", C.c_double), ("krylov_mmax", C.c_int),
+        ("cuda_stream", C.c_void_p), ("er_tree", C.c_int), ("D_er", C.c_int), ("init_state", C.c_int),
+        ("psi_el", C.POINTER(C.c_double)), ("record", C.c_int), ("max_record", C.c_int),
+        ("cluster_ctas", C.c_int), ("grid_ctas", C.c_int),
+    ]
+
+
+class ProblemC(C.Structure):
+    _fields_ = [
+        ("n_el", C.c_int), ("H_S", C.POINTER(C.c_double)), ("n_env", C.c_int), ("W_bar", C.POINTER(C.c_double)),
+        ("rc_coupling", C.POINTER(C.c_double)), ("chain_len", C.POINTER(C.c_int)),
+        ("chain_omega", C.POINTER(C.POINTER(C.c_double))), ("chain_hop", C.POINTER(C.POINTER(C.c_double))),
+        ("local_dim", C.POINTER(C.c_int)), ("bond_dim", C.POINTER(C.c_int)),
+    ]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n_nodes", C.c_int), ("pool_complex", C.c_longlong), ("max_node", C.c_int), ("max_bond", C.c_int),
+                ("instructions_per_step", C.c_int), ("work_complex_per_worker", C.c_longlong),
+                ("apply_flops_per_step", C.c_double), ("env_flops_per_step", C.c_double),
+                ("exponentials_per_step", C.c_int), ("env_updates_per_step", C.c_int),
+                ("n_bonds_written", C.c_int), ("bonds", C.c_int * 4096)]
+
+
+class Counters(C.Structure):
+    _fields_ = [("krylov_iters", C.c_longlong), ("applies", C.c_longlong), ("contraction_flops", C.c_double),
+                ("not_converged", C.c_longlong), ("steps", C.c_longlong)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_1710_01362_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        dp = C.POINTER(C.c_double)
+        L.ttns_last_error.restype = C.c_char_p
+        L.ttns_build_tree.argtypes = [C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(C.c_void_p)]
+        L.ttns_build_batch.argtypes = [C.c_int, C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(C.c_void_p)]
+        L.ttns_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
+        L.ttns_sync.argtypes = [C.c_void_p]
+        L.ttns_reduced_density_matrix.argtypes = [C.c_void_p, C.c_int, dp]
+        L.ttns_occupations.argtypes = [C.c_void_p, C.c_int, dp]
+        L.ttns_observables.argtypes = [C.c_void_p, C.c_int, dp, dp]
+        L.ttns_trajectory.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, C.POINTER(C.c_int)]
+        L.ttns_populations_device.argtypes = [C.c_void_p, C.c_void_p]
+        L.ttns_get_counters.argtypes = [C.c_void_p, C.POINTER(Counters)]
+        L.ttns_node_info.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_int)]
+        L.ttns_get_node.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_size_t]
+        L.ttns_save.argtypes = [C.c_void_p, C.c_char_p]
+        L.ttns_load_state.argtypes = [C.c_void_p, C.c_char_p]
+        L.ttns_free.argtypes = [C.c_void_p]
+        L.ttns_free.restype = None
+        L.ttns_plan.argtypes = [C.c_int, C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(PlanInfo)]
+        L.ttns_chain_ohmic.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp, dp]
+        L.ttns_chain_from_modes.argtypes = [C.c_int, dp, dp, C.c_int, dp, dp, dp]
+        _lib = L
+    return _lib
+
+
+def _check(code: int) -> None:
+    if code != 0:
+        raise TTNSError(code, lib().ttns_last_error().decode())
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def chain_ohmic(alpha: float, omega_c: float, L: int):
+    rc = np.zeros(1)
+    on = np.zeros(L)
+    hop = np.zeros(max(L - 1, 1))
+    _check(lib().ttns_chain_ohmic(alpha, omega_c, L, _dptr(rc), _dptr(on), _dptr(hop)))
+    return float(rc[0]), on, hop[: L - 1]
+
+
+def chain_from_modes(omega, lam, L: int):
+    om = np.ascontiguousarray(omega, dtype=float)
+    la = np.ascontiguousarray(lam, dtype=float)
+    rc = np.zeros(1)
+    on = np.zeros(L)
+    hop = np.zeros(max(L - 1, 1))
+    _check(lib().ttns_chain_from_modes(om.size, _dptr(om), _dptr(la), L, _dptr(rc), _dptr(on), _dptr(hop)))
+    return float(rc[0]), on, hop[: L - 1]
+
+
+def chain_of(spectral, L: int):
+    if spectral[0] == "ohmic":
+        return chain_ohmic(spectral[1], spectral[2], L)
+    return chain_from_modes(spectral[1], spectral[2], L)
+
+
+def _cplx(a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+    return np.ascontiguousarray(a.view(np.float64).reshape(-1))
+
+
+class _ProblemKeep:
+    """Holds the numpy buffers a ProblemC points into."""
+
+    def __init__(self, problem):
+        p = problem
+        ne = p.n_el
+        self.H = _cplx(p.H_S)
+        self.W = _cplx(np.stack([e.W_bar for e in p.envs]))
+        chains = [chain_of(e.spectral, e.L) for e in p.envs]
+        self.rc = np.array([c[0] for c in chains], dtype=float)
+        self.L = np.array([e.L for e in p.envs], dtype=np.int32)
+        self.om = [np.ascontiguousarray(c[1], dtype=float) for c in chains]
+        self.hop = [np.ascontiguousarray(c[2] if len(c[2]) else np.zeros(1), dtype=float) for c in chains]
+        self.om_ptrs = (C.POINTER(C.c_double) * len(self.om))(*[_dptr(x) for x in self.om])
+        self.hop_ptrs = (C.POINTER(C.c_double) * len(self.hop))(*[_dptr(x) for x in self.hop])
+        self.d = np.array([e.d for e in p.envs], dtype=np.int32)
+        self.D = np.array([min(e.D, 64) for e in p.envs], dtype=np.int32)
+        self.c = ProblemC(ne, _dptr(self.H), len(p.envs), _dptr(self.W), _dptr(self.rc),
+                          self.L.ctypes.data_as(C.POINTER(C.c_int)), self.om_ptrs, self.hop_ptrs,
+                          self.d.ctypes.data_as(C.POINTER(C.c_int)), self.D.ctypes.data_as(C.POINTER(C.c_int)))
+
+
+def current_stream() -> Optional[int]:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def _options(p0, precision, record=False, max_record=0, stream=None, cluster_ctas=0, grid_ctas=0,
+             krylov_tol=0.0, krylov_mmax=0, keep=None):
+    psi = None
+    if p0.psi_el is not None:
+        arr = _cplx(p0.psi_el)
+        if keep is not None:
+            keep.append(arr)
+        psi = _dptr(arr)
+    return Options(precision, krylov_tol, krylov_mmax, stream, int(p0.er_tree), int(p0.D_er),
+                   int(p0.init_state), psi, int(record), int(max_record), cluster_ctas, grid_ctas)
+
+
+def plan(problems, precision: int = TTNS_MIXED, krylov_mmax: int = 0) -> dict:
+    """Host-only compile and table check; no GPU needed."""
+    probs = list(problems) if isinstance(problems, (list, tuple)) else [problems]
+    keep = [_ProblemKeep(p) for p in probs]
+    hold = []
+    opt = _options(probs[0], precision, keep=hold, krylov_mmax=krylov_mmax)
+    arr = (ProblemC * len(probs))(*[k.c for k in keep])
+    info = PlanInfo()
+    _check(lib().ttns_plan(len(probs), arr, C.byref(opt), C.byref(info)))
+    return {"n_nodes": info.n_nodes, "pool_complex": info.pool_complex, "max_node": info.max_node,
+            "max_bond": info.max_bond, "instructions_per_step": info.instructions_per_step,
+            "work_complex_per_worker": info.work_complex_per_worker,
+            "apply_flops_per_step": info.apply_flops_per_step, "env_flops_per_step": info.env_flops_per_step,
+            "exponentials_per_step": info.exponentials_per_step, "env_updates_per_step": info.env_updates_per_step,
+            "bonds": [info.bonds[i] for i in range(info.n_bonds_written)]}
+
+
+class Tree:
+    """A set of trees on the device (one tree, or a batch advanced together)."""
+
+    def __init__(self, problems, precision: int = TTNS_MIXED, record: bool = False, max_record: int = 0,
+                 stream: Optional[int] = None, cluster_ctas: int = 0, grid_ctas: int = 0,
+                 krylov_tol: float = 0.0, krylov_mmax: int = 0):
+        single = not isinstance(problems, (list, tuple))
+        probs = [problems] if single else list(problems)
+        self.problems = probs
+        p0 = probs[0]
+        self._keep = [_ProblemKeep(p) for p in probs]
+        psi = None
+        if p0.psi_el is not None:
+            self._psi = _cplx(p0.psi_el)
+            psi = _dptr(self._psi)
+        if stream is None:
+            stream = current_stream()
+        self.opt = Options(precision, krylov_tol, krylov_mmax, stream, int(p0.er_tree), int(p0.D_er),
+                           int(p0.init_state), psi, int(record), int(max_record), cluster_ctas, grid_ctas)
+        h = C.c_void_p()
+        arr = (ProblemC * len(probs))(*[k.c for k in self._keep])
+        if len(probs) == 1:
+            _check(lib().ttns_build_tree(arr, C.byref(self.opt), C.byref(h)))
+        else:
+            _check(lib().ttns_build_batch(len(probs), arr, C.byref(self.opt), C.byref(h)))
+        self.h = h
+        self.n_trees = len(probs)
+
+    def close(self) -> None:
+        if self.h:
+            lib().ttns_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, dt: float, n: int = 1) -> None:
+        _check(lib().ttns_step(self.h, dt, n))
+
+    def sync(self) -> None:
+        _check(lib().ttns_sync(self.h))
+
+    def rho(self, k: int = 0) -> np.ndarray:
+        ne = self.problems[k].n_el
+        out = np.zeros(2 * ne * ne)
+        _check(lib().ttns_reduced_density_matrix(self.h, k, _dptr(out)))
+        return out.view(np.complex128).reshape(ne, ne)
+
+    def populations(self, k: int = 0) -> np.ndarray:
+        return np.real(np.diag(self.rho(k))).copy()
+
+    def occupations(self, k: int = 0) -> np.ndarray:
+        n = sum(e.L for e in self.problems[k].envs)
+        out = np.zeros(n)
+        _check(lib().ttns_occupations(self.h, k, _dptr(out)))
+        return out
+
+    def observables(self, k: int = 0):
+        nrm = C.c_double()
+        en = C.c_double()
+        _check(lib().ttns_observables(self.h, k, C.byref(nrm), C.byref(en)))
+        return nrm.value, en.value
+
+    def trajectory(self, k: int = 0, max_steps: int = 100000) -> np.ndarray:
+        ne = self.problems[k].n_el
+        out = np.zeros(2 * max_steps * ne * ne)
+        n = C.c_int()
+        _check(lib().ttns_trajectory(self.h, k, _dptr(out), max_steps, C.byref(n)))
+        return out[: 2 * n.value * ne * ne].view(np.complex128).reshape(n.value, ne, ne)
+
+    def populations_device(self, dev_ptr: int) -> None:
+        _check(lib().ttns_populations_device(self.h, C.c_void_p(dev_ptr)))
+
+    def counters(self) -> dict:
+        c = Counters()
+        _check(lib().ttns_get_counters(self.h, C.byref(c)))
+        return {"krylov_iters": c.krylov_iters, "applies": c.applies, "contraction_flops": c.contraction_flops,
+                "not_converged": c.not_converged, "steps": c.steps}
+
+    def n_nodes(self, k: int = 0) -> int:
+        n = C.c_int()
+        _check(lib().ttns_node_info(self.h, k, -1, None, None, C.byref(n)))
+        return n.value
+
+    def node(self, v: int, k: int = 0) -> np.ndarray:
+        nl = C.c_int()
+        dims = (C.c_int * 8)()
+        _check(lib().ttns_node_info(self.h, k, v, C.byref(nl), dims, None))
+        shape = tuple(dims[i] for i in range(nl.value))
+        n = int(np.prod(shape))
+        out = np.zeros(2 * n)
+        _check(lib().ttns_get_node(self.h, k, v, _dptr(out), n))
+        return out.view(np.complex128).reshape(shape)
+
+    def save(self, path: str) -> None:
+        _check(lib().ttns_save(self.h, path.encode()))
+
+    def load_state(self, path: str) -> None:
+        _check(lib().ttns_load_state(self.h, path.encode()))
