@@ -67,7 +67,12 @@ typedef struct {
   int record;            /* 1: keep rho_S after every step in a device trajectory buffer */
   int max_record;        /* capacity of that buffer in steps (0 -> 4096) */
   int cluster_ctas;      /* CTAs per cluster team (0 -> 16) */
-  int grid_ctas;         /* CTAs of the persistent grid (0 -> one per SM) */
+  int grid_ctas;         /* CTAs of the persistent grid (0 -> as many as can be co-resident) */
+  int grid_threshold;    /* single tree: tensors with at least this many elements are handled by the
+                            whole grid, smaller ones by one cluster (0 -> 65536) */
+  long long spin_limit;  /* bound of every device-side wait, in SM clock cycles (0 -> 2e10);
+                            a wait that runs out sets TTNS_E_TIMEOUT */
+  int profile;           /* 1: accumulate per-op device time (see ttns_counters) */
 } ttns_options;
 
 /* One tree's Hamiltonian (Eq. 2) and truncation.
@@ -162,6 +167,11 @@ typedef struct {
   double contraction_flops;
   long long not_converged;
   long long steps;
+  /* with ttns_options.profile = 1: device time per op kind (0 forward exponential,
+   * 1 QR, 2 environment update, 3 bond exponential, 4 absorb, 5 record) and team
+   * (0 whole grid, 1 cluster), in seconds at the SM clock rate, and op counts */
+  double op_seconds[6][2];
+  long long op_count[6][2];
 } ttns_counters;
 ttns_status ttns_get_counters(ttns_tree* tree, ttns_counters* out);
 
@@ -174,6 +184,13 @@ ttns_status ttns_get_node(ttns_tree* tree, int tree_idx, int node, double* out, 
 /* Writes / reads a checkpoint: every tree's tensors, time and step count. */
 ttns_status ttns_save(ttns_tree* tree, const char* path);
 ttns_status ttns_load_state(ttns_tree* tree, const char* path);
+
+/* Self-test of the device-side bounded wait (no counterpart in the paper: failure
+ * handling of this library).  With spin_limit > 0, a two-CTA barrier is launched in
+ * which one CTA never arrives; the other gives up after spin_limit SM cycles and
+ * *device_status receives TTNS_E_TIMEOUT.  With spin_limit == 0 both arrive and
+ * *device_status receives TTNS_OK.  Uses the legacy default stream. */
+ttns_status ttns_selftest_wait_timeout(long long spin_limit, int* device_status);
 
 const char* ttns_last_error(void);
 void ttns_free(ttns_tree* tree);

@@ -23,7 +23,11 @@ Krylov exponential  y = exp(-i s H) v  (s = time / hbar, any sign)
     Lanczos with classical Gram-Schmidt run twice against all previous vectors
     (full re-orthogonalisation).  After step j the tridiagonal T is
     exponentiated through its eigen-decomposition; the step stops when
-    beta_{j+1} |e_j^T exp(-i s T) e_0| <= tol (Saad's estimate) or j + 1 == mmax.
+    beta_{j+1} |e_j^T exp(-i s T) e_0| <= tol (Saad's estimate).  If mmax steps
+    do not reach tol, the time is split: the largest s / 2^k whose estimate on
+    the same Krylov space reaches tol is taken, and a new space is built from the
+    result for the remaining time (long chains whose onsite energies grow along
+    the chain have local Hamiltonians too wide for one space of dimension 30).
 """
 from __future__ import annotations
 
@@ -106,14 +110,11 @@ def expm_tridiag_e0(alpha: np.ndarray, beta: np.ndarray, s: float) -> np.ndarray
     return S @ (np.exp(-1j * s * w) * S[0, :])
 
 
-def expm_lanczos(apply_H, v: np.ndarray, s: float, tol: float = KRYLOV_TOL,
-                 mmax: int = KRYLOV_MMAX, stats: dict | None = None) -> np.ndarray:
-    """y = exp(-i s H) v for Hermitian H given as a matrix-free apply_H(x)."""
-    shape = v.shape
-    v = np.asarray(v, dtype=complex).reshape(-1)
+def _lanczos_chunk(apply_H, v: np.ndarray, shape, s: float, tol: float, mmax: int, stats):
+    """One Krylov space from v.  Returns (y, s_done): y = exp(-i s_done H) v with
+    s_done = s when the estimate reaches tol within mmax steps, else the largest
+    s / 2^k whose estimate on the same space reaches tol."""
     beta0 = np.linalg.norm(v)
-    if beta0 == 0.0:
-        return v.reshape(shape).copy()
     n = v.size
     mmax = min(mmax, n)
     Qk = np.zeros((mmax, n), dtype=complex)
@@ -122,6 +123,8 @@ def expm_lanczos(apply_H, v: np.ndarray, s: float, tol: float = KRYLOV_TOL,
     Qk[0] = v / beta0
     u = None
     m = 0
+    err = 0.0
+    b = 0.0
     for j in range(mmax):
         w = np.asarray(apply_H(Qk[j].reshape(shape)), dtype=complex).reshape(-1)
         alpha[j] = np.real(np.vdot(Qk[j], w))
@@ -136,13 +139,43 @@ def expm_lanczos(apply_H, v: np.ndarray, s: float, tol: float = KRYLOV_TOL,
         m = j + 1
         err = b * abs(u[j])
         if err <= tol or j + 1 == mmax:
-            if err > tol and j + 1 < n:
-                if stats is not None:
-                    stats["not_converged"] = stats.get("not_converged", 0) + 1
             break
         Qk[j + 1] = w / b
     if stats is not None:
         stats["krylov_iters"] = stats.get("krylov_iters", 0) + m
         stats["applies"] = stats.get("applies", 0) + m
-    y = beta0 * (u @ Qk[:m])
+    s_done = s
+    if err > tol and m < n:
+        # time-substep on the same Krylov space: the largest s / 2^k that converges
+        s_done = s
+        for _ in range(30):
+            s_done = 0.5 * s_done
+            u = expm_tridiag_e0(alpha[:m], beta[: m - 1], s_done)
+            if b * abs(u[m - 1]) <= tol:
+                break
+    return beta0 * (u @ Qk[:m]), s_done
+
+
+def expm_lanczos(apply_H, v: np.ndarray, s: float, tol: float = KRYLOV_TOL,
+                 mmax: int = KRYLOV_MMAX, stats: dict | None = None) -> np.ndarray:
+    """y = exp(-i s H) v for Hermitian H given as a matrix-free apply_H(x).
+
+    When mmax Lanczos steps do not reach the tolerance for the whole time s, the
+    step is split: the largest s / 2^k that converges on the current Krylov
+    space is taken, and a new space is built from the result for the rest."""
+    shape = v.shape
+    y = np.asarray(v, dtype=complex).reshape(-1)
+    if np.linalg.norm(y) == 0.0:
+        return y.reshape(shape).copy()
+    remaining = s
+    for chunk in range(64):
+        y, done = _lanczos_chunk(apply_H, y, shape, remaining, tol, mmax, stats)
+        if done == remaining:
+            break
+        remaining = remaining - done
+        if stats is not None:
+            stats["substeps"] = stats.get("substeps", 0) + 1
+    else:
+        if stats is not None:
+            stats["not_converged"] = stats.get("not_converged", 0) + 1
     return y.reshape(shape)

@@ -14,12 +14,13 @@
 
 namespace ttns {
 cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster, cudaStream_t stream);
-cudaError_t max_grid_for(int cluster, int* grid);
+cudaError_t max_grid_for(int cluster, long long smem_bytes, int* grid);
 cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double* partials,
                            int nblocks, double* out, cudaStream_t st);
 cudaError_t launch_energy(const KernelParams& P, int node, int terms, int n2, double* partials, int nblocks,
                           double* out, cudaStream_t st);
 cudaError_t launch_occ(const double2* dens, int d, double* out, cudaStream_t st);
+cudaError_t launch_wait_selftest(Ctl* ctl, long long spin_limit, int skip, cudaStream_t st);
 }  // namespace ttns
 
 using namespace ttns;
@@ -190,7 +191,8 @@ static ttns_status check_tables(const Compiled& C, int mmax, long long kvec, lon
     if (I.op == OP_FWD || I.op == OP_BOND || I.op == OP_ENV) {
       if (I.terms < 0 || I.terms >= (int)C.lists.size()) return fail(TTNS_E_INVALID, "table: term list");
       const TermList& L = C.lists[I.terms];
-      if (L.first < 0 || L.first + L.count > (int)C.terms.size() || L.n2 > n_tmp || L.n2 > L.count)
+      if (L.first < 0 || L.first + L.count > (int)C.terms.size() || L.n2 > n_tmp || L.n2 > L.count ||
+          L.count > TTNS_MAX_TERMS)
         return fail(TTNS_E_INVALID, "table: term range");
       for (int k = 0; k < L.count; ++k) {
         const Term& T = C.terms[L.first + k];
@@ -203,7 +205,8 @@ static ttns_status check_tables(const Compiled& C, int mmax, long long kvec, lon
     }
     if (I.op == OP_ENV) {
       if (I.leg < 0 || I.leg >= nd.nl || I.D != nd.dims[I.leg]) return fail(TTNS_E_INVALID, "table: env leg");
-      if (I.chan_first < 0 || I.chan_first + I.nchan > (int)C.chans.size()) return fail(TTNS_E_INVALID, "table: chans");
+      if (I.chan_first < 0 || I.chan_first + I.nchan > (int)C.chans.size() || I.nchan > 16)
+        return fail(TTNS_E_INVALID, "table: chans");
       for (int b = 0; b < I.nchan; ++b)
         if (!check_factor(C.chans[I.chan_first + b], nd)) return fail(TTNS_E_INVALID, "table: channel factor");
       if (!in_pool(I.env_out, (long long)(1 + I.nchan) * I.D * I.D)) return fail(TTNS_E_INVALID, "table: env out");
@@ -258,7 +261,8 @@ static ttns_status device_init(ttns_tree* t) {
   t->cluster = o.cluster_ctas > 0 ? o.cluster_ctas : 16;
   if (t->cluster > 16) return fail(TTNS_E_INVALID, "cluster_ctas must be <= 16");
   int maxgrid = 0;
-  CUDA_TRY(max_grid_for(t->cluster, &maxgrid));
+  const long long smem_bytes = 160 * 1024;
+  CUDA_TRY(max_grid_for(t->cluster, smem_bytes, &maxgrid));
   if (maxgrid < t->cluster) return fail(TTNS_E_CUDA, "no co-resident cluster of the requested size");
   int grid = o.grid_ctas > 0 ? o.grid_ctas : maxgrid;
   grid = std::min(grid, maxgrid);
@@ -331,7 +335,9 @@ static ttns_status device_init(ttns_tree* t) {
   P.tol = o.krylov_tol > 0 ? o.krylov_tol : 1e-12;
   P.mmax = mmax;
   P.cluster_ctas = t->cluster;
-  P.spin_limit = 20LL * 1000 * 1000 * 1000;  // clock cycles (~10 s)
+  P.spin_limit = o.spin_limit > 0 ? o.spin_limit : 20LL * 1000 * 1000 * 1000;  // SM clock cycles (~10 s)
+  P.profile = o.profile;
+  P.smem_bytes = smem_bytes;
   // initial environment pass
   CUDA_TRY(launch_sweep(P, 0, t->grid, t->cluster, t->stream));
   CUDA_TRY(cudaStreamSynchronize(t->stream));
@@ -348,6 +354,7 @@ static ttns_status compile_only(int n_trees, const ttns_problem* probs, const tt
   if (o.krylov_mmax < 0 || o.krylov_mmax > TTNS_KMAX) return fail(TTNS_E_INVALID, "krylov_mmax out of range (0..32)");
   if (o.krylov_tol < 0) return fail(TTNS_E_INVALID, "krylov_tol < 0");
   if (o.max_record < 0) return fail(TTNS_E_INVALID, "max_record < 0");
+  if (o.grid_threshold < 0 || o.spin_limit < 0) return fail(TTNS_E_INVALID, "negative grid_threshold or spin_limit");
   std::vector<TreeInput> ins(n_trees);
   for (int i = 0; i < n_trees; ++i) {
     ttns_status s = validate(&probs[i], &o, &ins[i]);
@@ -358,7 +365,8 @@ static ttns_status compile_only(int n_trees, const ttns_problem* probs, const tt
   t->batched = n_trees > 1;
   t->stream = (cudaStream_t)o.cuda_stream;
   try {
-    t->C = compile_trees(ins, t->batched, /*grid_threshold=*/65536, o.max_record > 0 ? o.max_record : 4096, o.record);
+    t->C = compile_trees(ins, t->batched, o.grid_threshold > 0 ? o.grid_threshold : 65536,
+                         o.max_record > 0 ? o.max_record : 4096, o.record);
   } catch (const std::exception& e) {
     return fail(TTNS_E_INVALID, std::string("model: ") + e.what());
   }
@@ -599,6 +607,14 @@ extern "C" ttns_status ttns_get_counters(ttns_tree* t, ttns_counters* out) {
   out->contraction_flops = h.flops;
   out->not_converged = (long long)h.not_converged;
   out->steps = (long long)h.steps;
+  int khz = 0;
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, 0);
+  const double hz = khz > 0 ? khz * 1e3 : 1.9e9;
+  for (int op = 0; op < 6; ++op)
+    for (int k = 0; k < 2; ++k) {
+      out->op_seconds[op][k] = h.prof_cycles[op][k] / hz;
+      out->op_count[op][k] = (long long)h.prof_count[op][k];
+    }
   return TTNS_OK;
 }
 
@@ -710,5 +726,21 @@ extern "C" ttns_status ttns_chain_from_modes(int n_modes, const double* omega, c
   if (L < 1 || L > n_modes) return fail(TTNS_E_INVALID, "L must be in 1..n_modes");
   if (!chain_from_modes(n_modes, omega, lambda, L, rc, onsite, hop))
     return fail(TTNS_E_INVALID, "Lanczos breakdown: fewer distinct modes than sites");
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_selftest_wait_timeout(long long spin_limit, int* device_status) {
+  if (!device_status) return fail(TTNS_E_INVALID, "NULL argument");
+  Ctl* ctl = nullptr;
+  CUDA_TRY(cudaMalloc(&ctl, sizeof(Ctl)));
+  cudaError_t e = cudaMemset(ctl, 0, sizeof(Ctl));
+  const int skip = spin_limit > 0 ? 1 : 0;
+  if (e == cudaSuccess) e = launch_wait_selftest(ctl, spin_limit > 0 ? spin_limit : 2000000000LL, skip, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  Ctl h{};
+  if (e == cudaSuccess) e = cudaMemcpy(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+  cudaFree(ctl);
+  if (e != cudaSuccess) return fail(TTNS_E_CUDA, cudaGetErrorString(e));
+  *device_status = h.status;
   return TTNS_OK;
 }

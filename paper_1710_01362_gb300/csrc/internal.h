@@ -100,6 +100,8 @@ struct Ctl {
   unsigned long long steps;
   int err_where;       // op code of the first failure
   int err_node;
+  unsigned long long prof_cycles[8][2];  // per op code and team kind (rank-0 CTA clock cycles)
+  unsigned long long prof_count[8][2];
 };
 
 struct KernelParams {
@@ -136,6 +138,8 @@ struct KernelParams {
   int mmax;
   int cluster_ctas;
   long long spin_limit;
+  int profile;
+  long long smem_bytes;    // dynamic shared memory per CTA (operator matrices of one op)
 };
 
 }  // namespace ttns

@@ -50,6 +50,21 @@ __device__ __forceinline__ typename C2<T>::t ld(const double2* p) {
   return r;
 }
 template <typename T>
+__device__ __forceinline__ typename C2<T>::t cvt(double2 v) {
+  typename C2<T>::t r;
+  r.x = (T)v.x;
+  r.y = (T)v.y;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ typename C2<T>::t cvt(float2 v) {
+  typename C2<T>::t r;
+  r.x = (T)v.x;
+  r.y = (T)v.y;
+  return r;
+}
+
+template <typename T>
 __device__ __forceinline__ void cmac(typename C2<T>::t& acc, typename C2<T>::t a, typename C2<T>::t b) {
   acc.x = fma(a.x, b.x, acc.x);
   acc.x = fma(-a.y, b.y, acc.x);
@@ -189,29 +204,106 @@ __device__ __forceinline__ LegPos leg_pos(const NodeDesc& nd, int l, long long i
   return LegPos{idx - (long long)i * st, i};
 }
 
-template <typename T>
-__device__ __forceinline__ typename C2<T>::t mode_dot(const double2* pool_unused, const double2* M, int D,
-                                                      int i, const double2* x, long long base, int stride) {
-  typename C2<T>::t acc;
-  acc.x = 0;
-  acc.y = 0;
-  const double2* row = M + (long long)i * D;
-  for (int k = 0; k < D; ++k) cmac<T>(acc, ld<T>(row + k), ld<T>(x + base + (long long)k * stride));
-  return acc;
+// y_i = sum_k M[i][k] x[base + k*stride] with four independent accumulators.  M is a row
+// of a dims x dims matrix, either staged in shared memory (compute type) or in the pool.
+template <typename T, typename MT, typename XT>
+__device__ __forceinline__ typename C2<T>::t mode_dot(const MT* row, int D, const XT* x, long long base, int stride) {
+  using V = typename C2<T>::t;
+  V a0, a1, a2, a3;
+  a0.x = a0.y = a1.x = a1.y = a2.x = a2.y = a3.x = a3.y = (T)0;
+  const XT* xp = x + base;
+  int k = 0;
+  for (; k + 3 < D; k += 4) {
+    const V m0 = cvt<T>(row[k]), m1 = cvt<T>(row[k + 1]), m2 = cvt<T>(row[k + 2]), m3 = cvt<T>(row[k + 3]);
+    const V x0 = cvt<T>(xp[(long long)k * stride]), x1 = cvt<T>(xp[(long long)(k + 1) * stride]);
+    const V x2 = cvt<T>(xp[(long long)(k + 2) * stride]), x3 = cvt<T>(xp[(long long)(k + 3) * stride]);
+    cmac<T>(a0, m0, x0);
+    cmac<T>(a1, m1, x1);
+    cmac<T>(a2, m2, x2);
+    cmac<T>(a3, m3, x3);
+  }
+  for (; k < D; ++k) cmac<T>(a0, cvt<T>(row[k]), cvt<T>(xp[(long long)k * stride]));
+  a0.x += a1.x + (a2.x + a3.x);
+  a0.y += a1.y + (a2.y + a3.y);
+  return a0;
 }
 
-// Stage 1: tmp[t] = first factor of two-factor term t applied to x
+// Operator matrices of one op, staged once in dynamic shared memory in the compute type.
+// slot[t][f] gives the shared offset of factor f of term t (-1: read from the pool).
+extern __shared__ __align__(16) unsigned char dyn_smem[];
+struct StageTable {
+  int slot[TTNS_MAX_TERMS][2];
+  int chan[16];
+};
+
+template <typename T>
+__device__ void stage_matrices(const KernelParams& P, const NodeDesc& nd, const TermList& L, const Factor* chans,
+                               int nchan, StageTable& st) {
+  using V = typename C2<T>::t;
+  V* sm = reinterpret_cast<V*>(dyn_smem);
+  const long long cap = P.smem_bytes / (long long)sizeof(V);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long off = 0;
+    for (int t = 0; t < L.count && t < TTNS_MAX_TERMS; ++t) {
+      const Term& T_ = P.terms[L.first + t];
+      for (int f = 0; f < 2; ++f) {
+        st.slot[t][f] = -1;
+        if (f < T_.nf) {
+          const long long need = (long long)nd.dims[T_.f[f].leg] * nd.dims[T_.f[f].leg];
+          if (off + need <= cap) { st.slot[t][f] = (int)off; off += need; }
+        }
+      }
+    }
+    for (int b = 0; b < nchan && b < 16; ++b) {
+      st.chan[b] = -1;
+      const long long need = (long long)nd.dims[chans[b].leg] * nd.dims[chans[b].leg];
+      if (off + need <= cap) { st.chan[b] = (int)off; off += need; }
+    }
+  }
+  __syncthreads();
+  for (int t = 0; t < L.count && t < TTNS_MAX_TERMS; ++t) {
+    const Term& T_ = P.terms[L.first + t];
+    for (int f = 0; f < T_.nf; ++f) {
+      const int o = st.slot[t][f];
+      if (o < 0) continue;
+      const int n = nd.dims[T_.f[f].leg] * nd.dims[T_.f[f].leg];
+      const double2* src = P.pool + T_.f[f].mat;
+      for (int k = threadIdx.x; k < n; k += NT) sm[o + k] = cvt<T>(src[k]);
+    }
+  }
+  for (int b = 0; b < nchan && b < 16; ++b) {
+    const int o = st.chan[b];
+    if (o < 0) continue;
+    const int n = nd.dims[chans[b].leg] * nd.dims[chans[b].leg];
+    const double2* src = P.pool + chans[b].mat;
+    for (int k = threadIdx.x; k < n; k += NT) sm[o + k] = cvt<T>(src[k]);
+  }
+  __syncthreads();
+}
+
+template <typename T, typename XT>
+__device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, const NodeDesc& nd, const Factor& f,
+                                                        int slot, const XT* x, long long idx) {
+  const LegPos lp = leg_pos(nd, f.leg, idx);
+  const int D = nd.dims[f.leg];
+  if (slot >= 0) {
+    const typename C2<T>::t* sm = reinterpret_cast<const typename C2<T>::t*>(dyn_smem) + slot;
+    return mode_dot<T>(sm + lp.i * D, D, x, lp.base, nd.strides[f.leg]);
+  }
+  return mode_dot<T>(P.pool + f.mat + (long long)lp.i * D, D, x, lp.base, nd.strides[f.leg]);
+}
+
+// Stage 1: tmp[t] = first factor of two-factor term t applied to x (tmp in the compute type)
 template <typename T>
 __device__ void apply_stage1(const KernelParams& P, Team& tm, const NodeDesc& nd, const double2* x, const TermList& L,
-                             double2* tmp, long long tstride) {
-  const Term* terms = P.terms + L.first + (L.count - L.n2);
+                             typename C2<T>::t* tmp, long long tstride, const StageTable& st) {
+  const int n1 = L.count - L.n2;
+  const Term* terms = P.terms + L.first + n1;
   const long long N = nd.size;
   for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
     for (int t = 0; t < L.n2; ++t) {
-      const Factor f = terms[t].f[0];
-      LegPos lp = leg_pos(nd, f.leg, idx);
-      auto a = mode_dot<T>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, x, lp.base, nd.strides[f.leg]);
-      tmp[t * tstride + idx] = make_double2((double)a.x, (double)a.y);
+      tmp[t * tstride + idx] = factor_dot<T>(P, nd, terms[t].f[0], n1 + t < TTNS_MAX_TERMS ? st.slot[n1 + t][0] : -1, x, idx);
     }
   }
 }
@@ -219,24 +311,21 @@ __device__ void apply_stage1(const KernelParams& P, Team& tm, const NodeDesc& nd
 // Stage 2 value at idx: one-factor terms on x plus second factors on tmp
 template <typename T>
 __device__ __forceinline__ typename C2<T>::t apply_stage2_at(const KernelParams& P, const NodeDesc& nd, const double2* x,
-                                                            const TermList& L, const double2* tmp, long long tstride,
-                                                            long long idx) {
+                                                            const TermList& L, const typename C2<T>::t* tmp,
+                                                            long long tstride, long long idx, const StageTable& st) {
   typename C2<T>::t acc;
   acc.x = 0;
   acc.y = 0;
   const Term* terms = P.terms + L.first;
   const int n1 = L.count - L.n2;
   for (int t = 0; t < n1; ++t) {
-    const Factor f = terms[t].f[0];
-    LegPos lp = leg_pos(nd, f.leg, idx);
-    auto a = mode_dot<T>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, x, lp.base, nd.strides[f.leg]);
+    const auto a = factor_dot<T>(P, nd, terms[t].f[0], t < TTNS_MAX_TERMS ? st.slot[t][0] : -1, x, idx);
     acc.x += a.x;
     acc.y += a.y;
   }
   for (int t = 0; t < L.n2; ++t) {
-    const Factor f = terms[n1 + t].f[1];
-    LegPos lp = leg_pos(nd, f.leg, idx);
-    auto a = mode_dot<T>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, tmp + t * tstride, lp.base, nd.strides[f.leg]);
+    const auto a = factor_dot<T>(P, nd, terms[n1 + t].f[1], n1 + t < TTNS_MAX_TERMS ? st.slot[n1 + t][1] : -1,
+                                 tmp + t * tstride, idx);
     acc.x += a.x;
     acc.y += a.y;
   }
@@ -356,110 +445,134 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
   const long long kv = P.kvec;
   double2* x = P.pool + nd.off;
   double2* Kb = work;                           // K_1..K_mmax at Kb + (j-1)*kv
-  double2* tmp = work + (long long)P.mmax * kv;  // n_tmp temporaries
-  const double s = I.sign * tau / HBAR_EVFS;     // exp(-i s H)
+  auto* tmp = reinterpret_cast<typename C2<T>::t*>(work + (long long)P.mmax * kv);  // n_tmp temporaries
   auto Kp = [&](int j) -> double2* { return j == 0 ? x : Kb + (long long)(j - 1) * kv; };
-
-  double v[2];
-  v[0] = 0;
-  for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-    double2 a = x[idx];
-    v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
-  }
-  team_allreduce(tm, v, 1);
-  const double beta0 = sqrt(v[0]);
-  if (!(beta0 > 0.0)) {
-    if (!(beta0 == 0.0)) set_status(P.ctl, ST_NONFINITE, OP_FWD, I.node);
-    return;
-  }
-  if (threadIdx.x == 0) {
-    ks.scale[0] = 1.0 / beta0;
-    ks.beta[0] = 0.0;
-  }
-  __syncthreads();
-  int hint = P.mhist[I.hist];
-  if (hint < 2) hint = 2;
   const int mmax = min(P.mmax, (int)(N < (long long)TTNS_KMAX ? N : (long long)TTNS_KMAX));
+  __shared__ StageTable st;
+  stage_matrices<T>(P, nd, L, nullptr, 0, st);
+  // exp(-i s H): s = time / hbar with the op's sign.  If the Krylov space of dimension
+  // mmax does not reach the tolerance for the remaining time, the largest s / 2^k that
+  // does is taken on the same space and a new space is built for the rest.
+  double s_rem = I.sign * tau / HBAR_EVFS;
+  int total_m = 0;
   int m = 0;
-  bool conv = false;
-  for (int j = 0; j < mmax; ++j) {
-    double2* Kj = Kp(j);
-    double2* Kjm = j > 0 ? Kp(j - 1) : x;
-    double2* W = Kb + (long long)j * kv;  // slot of K_{j+1}
-    const double sj = ks.scale[j];
-    const double bj = ks.beta[j];
-    const double sjm = j > 0 ? ks.scale[j - 1] : 0.0;
-    if (L.n2 > 0) {
-      apply_stage1<T>(P, tm, nd, Kj, L, tmp, kv);
-      team_sync(tm);
-    }
-    double part[1] = {0.0};
+  for (int chunk = 0; chunk < 64; ++chunk) {
+    double v[1];
+    v[0] = 0;
     for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-      auto a = apply_stage2_at<T>(P, nd, Kj, L, tmp, kv, idx);
-      double2 kj = Kj[idx];
-      double wr = sj * (double)a.x, wi = sj * (double)a.y;
-      if (j > 0) {
-        double2 km = Kjm[idx];
-        wr = fma(-bj * sjm, km.x, wr);
-        wi = fma(-bj * sjm, km.y, wi);
-      }
-      W[idx] = make_double2(wr, wi);
-      part[0] = fma(kj.x, wr, fma(kj.y, wi, part[0]));  // Re(conj(K_j) w)
+      const double2 a = x[idx];
+      v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
     }
-    team_allreduce(tm, part, 1);
-    const double aj = part[0] * sj;
-    part[0] = 0.0;
-    for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-      double2 kj = Kj[idx];
-      double2 w = W[idx];
-      w.x = fma(-aj * sj, kj.x, w.x);
-      w.y = fma(-aj * sj, kj.y, w.y);
-      W[idx] = w;
-      part[0] = fma(w.x, w.x, fma(w.y, w.y, part[0]));
+    team_allreduce(tm, v, 1);
+    const double beta0 = sqrt(v[0]);
+    if (!(beta0 > 0.0)) {
+      if (!(beta0 == 0.0)) set_status(P.ctl, ST_NONFINITE, I.op, I.node);
+      break;
     }
-    team_allreduce(tm, part, 1);
-    const double bnext = sqrt(part[0]);
     if (threadIdx.x == 0) {
-      ks.alpha[j] = aj;
-      ks.beta[j + 1] = bnext;
-      ks.scale[j + 1] = bnext > 0.0 ? 1.0 / bnext : 0.0;
+      ks.scale[0] = 1.0 / beta0;
+      ks.beta[0] = 0.0;
     }
     __syncthreads();
-    m = j + 1;
-    if (m >= hint - 1 || m == mmax || !(bnext > 0.0)) {
-      if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s, ks.ure, ks.uim);
-      __syncthreads();
-      const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);
-      const double err = bnext * um;
-      if (!(err == err)) {
-        set_status(P.ctl, ST_NONFINITE, I.op, I.node);
-        conv = true;
-      } else if (err <= P.tol || !(bnext > 0.0)) {
-        conv = true;
+    int hint = P.mhist[I.hist];
+    if (hint < 2) hint = 2;
+    m = 0;
+    bool conv = false;
+    double bnext = 0.0;
+    for (int j = 0; j < mmax; ++j) {
+      double2* Kj = Kp(j);
+      double2* Kjm = j > 0 ? Kp(j - 1) : x;
+      double2* W = Kb + (long long)j * kv;  // slot of K_{j+1}
+      const double sj = ks.scale[j];
+      const double bj = ks.beta[j];
+      const double sjm = j > 0 ? ks.scale[j - 1] : 0.0;
+      if (L.n2 > 0) {
+        apply_stage1<T>(P, tm, nd, Kj, L, tmp, kv, st);
+        team_sync(tm);
       }
-      if (conv || m == mmax) break;
+      double part[1] = {0.0};
+      for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+        const auto a = apply_stage2_at<T>(P, nd, Kj, L, tmp, kv, idx, st);
+        const double2 kj = Kj[idx];
+        double wr = sj * (double)a.x, wi = sj * (double)a.y;
+        if (j > 0) {
+          const double2 km = Kjm[idx];
+          wr = fma(-bj * sjm, km.x, wr);
+          wi = fma(-bj * sjm, km.y, wi);
+        }
+        W[idx] = make_double2(wr, wi);
+        part[0] = fma(kj.x, wr, fma(kj.y, wi, part[0]));  // Re(conj(K_j) w)
+      }
+      team_allreduce(tm, part, 1);
+      const double aj = part[0] * sj;
+      part[0] = 0.0;
+      for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+        const double2 kj = Kj[idx];
+        double2 w = W[idx];
+        w.x = fma(-aj * sj, kj.x, w.x);
+        w.y = fma(-aj * sj, kj.y, w.y);
+        W[idx] = w;
+        part[0] = fma(w.x, w.x, fma(w.y, w.y, part[0]));
+      }
+      team_allreduce(tm, part, 1);
+      bnext = sqrt(part[0]);
+      if (threadIdx.x == 0) {
+        ks.alpha[j] = aj;
+        ks.beta[j + 1] = bnext;
+        ks.scale[j + 1] = bnext > 0.0 ? 1.0 / bnext : 0.0;
+      }
+      __syncthreads();
+      m = j + 1;
+      if (m >= hint - 1 || m == mmax || !(bnext > 0.0)) {
+        if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s_rem, ks.ure, ks.uim);
+        __syncthreads();
+        const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);
+        const double err = bnext * um;
+        if (!(err == err)) {
+          set_status(P.ctl, ST_NONFINITE, I.op, I.node);
+          conv = true;
+        } else if (err <= P.tol || !(bnext > 0.0)) {
+          conv = true;
+        }
+        if (conv || m == mmax) break;
+      }
     }
-  }
-  if (!conv && tm.rank == 0 && threadIdx.x == 0) atomicAdd(&P.ctl->not_converged, 1ull);
-  // y = beta0 * sum_k u_k q_k written over x (each thread reads its own K_0 = x entries first)
-  for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-    double yr = 0.0, yi = 0.0;
-    for (int k = 0; k < m; ++k) {
-      double2 q = Kp(k)[idx];
-      const double sc = beta0 * ks.scale[k];
-      const double cr = ks.ure[k] * sc, ci = ks.uim[k] * sc;
-      yr = fma(cr, q.x, fma(-ci, q.y, yr));
-      yi = fma(cr, q.y, fma(ci, q.x, yi));
+    total_m += m;
+    double s_done = s_rem;
+    if (!conv && m < N) {
+      // largest s_rem / 2^k that converges on this space (same decision on every CTA)
+      for (int k = 0; k < 30; ++k) {
+        s_done *= 0.5;
+        if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s_done, ks.ure, ks.uim);
+        __syncthreads();
+        const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);
+        __syncthreads();
+        if (bnext * um <= P.tol) break;
+      }
     }
-    x[idx] = make_double2(yr, yi);
+    // y = beta0 * sum_k u_k q_k written over x (each thread reads its own K_0 = x entries first)
+    for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+      double yr = 0.0, yi = 0.0;
+      for (int k = 0; k < m; ++k) {
+        const double2 q = Kp(k)[idx];
+        const double sc = beta0 * ks.scale[k];
+        const double cr = ks.ure[k] * sc, ci = ks.uim[k] * sc;
+        yr = fma(cr, q.x, fma(-ci, q.y, yr));
+        yi = fma(cr, q.y, fma(ci, q.x, yi));
+      }
+      x[idx] = make_double2(yr, yi);
+    }
+    team_sync(tm);
+    if (conv || m >= N || s_done == s_rem) break;
+    s_rem -= s_done;
+    if (chunk == 63 && tm.rank == 0 && threadIdx.x == 0) atomicAdd(&P.ctl->not_converged, 1ull);
   }
   if (tm.rank == 0 && threadIdx.x == 0) {
     P.mhist[I.hist] = m;
-    atomicAdd(&P.ctl->krylov_iters, (unsigned long long)m);
-    atomicAdd(&P.ctl->applies, (unsigned long long)m);
-    atomicAdd(&P.ctl->flops, I.flops * m);
+    atomicAdd(&P.ctl->krylov_iters, (unsigned long long)total_m);
+    atomicAdd(&P.ctl->applies, (unsigned long long)total_m);
+    atomicAdd(&P.ctl->flops, I.flops * total_m);
   }
-  team_sync(tm);
 }
 
 // ------------------------------------------------------------------ Householder QR
@@ -720,7 +833,7 @@ __device__ void op_absorb(const KernelParams& P, Team& tm, const Instr& I, doubl
   const int l = I.leg;
   for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
     LegPos lp = leg_pos(nd, l, idx);
-    auto a = mode_dot<double>(P.pool, R, nd.dims[l], lp.i, A, lp.base, nd.strides[l]);
+    auto a = mode_dot<double>(R + (long long)lp.i * nd.dims[l], nd.dims[l], A, lp.base, nd.strides[l]);
     work[idx] = a;
   }
   team_sync(tm);
@@ -738,22 +851,23 @@ __device__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2*
   const long long N = nd.size;
   const long long kv = P.kvec;
   const double2* Q = P.pool + nd.off;
-  double2* tmp = work + (long long)P.mmax * kv;
+  auto* tmp = reinterpret_cast<typename C2<T>::t*>(work + (long long)P.mmax * kv);
   double2* Y = work;  // Y_0 .. Y_nchan at work + b*kv (fits: 1 + nchan <= mmax)
   const int l = I.leg;
   const int D = I.D;
   const int nb = 1 + I.nchan;
+  __shared__ StageTable st;
+  stage_matrices<T>(P, nd, L, P.chans + I.chan_first, I.nchan, st);
   if (L.n2 > 0) {
-    apply_stage1<T>(P, tm, nd, Q, L, tmp, kv);
+    apply_stage1<T>(P, tm, nd, Q, L, tmp, kv, st);
     team_sync(tm);
   }
   for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-    auto a = apply_stage2_at<T>(P, nd, Q, L, tmp, kv, idx);
+    auto a = apply_stage2_at<T>(P, nd, Q, L, tmp, kv, idx, st);
     Y[idx] = make_double2((double)a.x, (double)a.y);
     for (int b = 0; b < I.nchan; ++b) {
       const Factor f = P.chans[I.chan_first + b];
-      LegPos lp = leg_pos(nd, f.leg, idx);
-      auto c = mode_dot<T>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, Q, lp.base, nd.strides[f.leg]);
+      auto c = factor_dot<T>(P, nd, f, b < 16 ? st.chan[b] : -1, Q, idx);
       Y[(long long)(1 + b) * kv + idx] = make_double2((double)c.x, (double)c.y);
     }
   }
@@ -762,7 +876,7 @@ __device__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2*
   const long long rows = N / D;
   const int nval = nb * D * D;
   double* part = team_partials(tm);
-  const long long st = nd.strides[l];
+  const long long lst = nd.strides[l];
   // rows split across CTAs in contiguous chunks; each thread owns output values
   const long long chunk = (rows + tm.size - 1) / tm.size;
   const long long r_begin = (long long)tm.rank * chunk;
@@ -779,10 +893,10 @@ __device__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2*
       s.y = 0;
       const long long r1 = min(r_end, r0 + 64);
       for (long long r = r0; r < r1; ++r) {
-        const long long p = r / st, q = r - p * st;
-        const long long base = p * D * st + q;
-        auto qa = ld<T>(Q + base + (long long)a * st);
-        auto y = ld<T>(Yb + base + (long long)a2 * st);
+        const long long p = r / lst, q = r - p * lst;
+        const long long base = p * D * lst + q;
+        auto qa = ld<T>(Q + base + (long long)a * lst);
+        auto y = ld<T>(Yb + base + (long long)a2 * lst);
         s.x = fma(qa.x, y.x, fma(qa.y, y.y, s.x));
         s.y = fma(qa.x, y.y, fma(-qa.y, y.x, s.y));
       }
@@ -833,7 +947,25 @@ __device__ void op_record(const KernelParams& P, Team& tm, const Instr& I, int* 
 
 // ------------------------------------------------------------------ interpreter
 template <typename T>
+__device__ void exec_op(const KernelParams& P, Team& tm, const Instr& I, double2* work);
+
+template <typename T>
 __device__ void exec(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
+  if (!P.profile) {
+    exec_op<T>(P, tm, I, work);
+    return;
+  }
+  const long long t0 = clock64();
+  exec_op<T>(P, tm, I, work);
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    const long long dt = clock64() - t0;
+    atomicAdd(&P.ctl->prof_cycles[I.op][tm.kind], (unsigned long long)dt);
+    atomicAdd(&P.ctl->prof_count[I.op][tm.kind], 1ull);
+  }
+}
+
+template <typename T>
+__device__ void exec_op(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
   const double tau = 0.5 * P.dt;
   switch (I.op) {
     case OP_FWD:
@@ -992,8 +1124,12 @@ __global__ void k_energy_partial(KernelParams P, int node, int terms, double* pa
   const double2* x = P.pool + nd.off;
   const long long N = nd.size;
   double e = 0, nn = 0;
+  __shared__ StageTable st;
+  if (threadIdx.x == 0)
+    for (int t = 0; t < TTNS_MAX_TERMS; ++t) st.slot[t][0] = st.slot[t][1] = -1;
+  __syncthreads();
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (long long)gridDim.x * blockDim.x) {
-    auto a = apply_stage2_at<double>(P, nd, x, L, P.work + (long long)P.mmax * P.kvec, P.kvec, idx);
+    auto a = apply_stage2_at<double>(P, nd, x, L, P.work + (long long)P.mmax * P.kvec, P.kvec, idx, st);
     double2 v = x[idx];
     e = fma(v.x, a.x, fma(v.y, a.y, e));
     nn = fma(v.x, v.x, fma(v.y, v.y, nn));
@@ -1022,10 +1158,23 @@ __global__ void k_stage1(KernelParams P, int node, int terms) {
     for (int t = 0; t < L.n2; ++t) {
       const Factor f = tl[t].f[0];
       LegPos lp = leg_pos(nd, f.leg, idx);
-      auto a = mode_dot<double>(P.pool, P.pool + f.mat, nd.dims[f.leg], lp.i, x, lp.base, nd.strides[f.leg]);
+      auto a = mode_dot<double>(P.pool + f.mat + (long long)lp.i * nd.dims[f.leg], nd.dims[f.leg], x, lp.base,
+                                nd.strides[f.leg]);
       tmp[t * P.kvec + idx] = a;
     }
   }
+}
+
+// Self-test of the bounded wait: two CTAs; with `skip` set the second CTA never
+// arrives at the barrier, so the first one must give up after spin_limit cycles.
+__global__ void k_wait_selftest(Ctl* ctl, long long spin_limit, int skip) {
+  if (skip && blockIdx.x == 1) return;
+  grid_sync(ctl, spin_limit);
+}
+
+cudaError_t launch_wait_selftest(Ctl* ctl, long long spin_limit, int skip, cudaStream_t st) {
+  void* args[] = {&ctl, &spin_limit, &skip};
+  return cudaLaunchCooperativeKernel((void*)k_wait_selftest, dim3(2), dim3(NT), args, 0, st);
 }
 
 // ------------------------------------------------------------------ host launch helpers
@@ -1050,10 +1199,12 @@ cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem_bytes);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = (size_t)P.smem_bytes;
   cfg.stream = stream;
   cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -1067,12 +1218,15 @@ cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster
   return cudaLaunchKernelEx(&cfg, k_sweep, P, phase);
 }
 
-cudaError_t max_grid_for(int cluster, int* grid) {
+cudaError_t max_grid_for(int cluster, long long smem_bytes, int* grid) {
   cudaError_t e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cluster);
   cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = (size_t)smem_bytes;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
   at[0].val.clusterDim.x = cluster;

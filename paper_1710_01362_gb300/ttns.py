@@ -24,7 +24,7 @@ EXPORTS = [
     "ttns_build_tree", "ttns_build_batch", "ttns_step", "ttns_sync", "ttns_reduced_density_matrix",
     "ttns_occupations", "ttns_observables", "ttns_trajectory", "ttns_populations_device", "ttns_get_counters",
     "ttns_node_info", "ttns_get_node", "ttns_save", "ttns_load_state", "ttns_last_error", "ttns_free",
-    "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan",
+    "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan", "ttns_selftest_wait_timeout",
 ]
 
 
@@ -39,7 +39,8 @@ class Options(C.Structure):
         ("precision", C.c_int), ("krylov_tol", C.c_double), ("krylov_mmax", C.c_int),
         ("cuda_stream", C.c_void_p), ("er_tree", C.c_int), ("D_er", C.c_int), ("init_state", C.c_int),
         ("psi_el", C.POINTER(C.c_double)), ("record", C.c_int), ("max_record", C.c_int),
-        ("cluster_ctas", C.c_int), ("grid_ctas", C.c_int),
+        ("cluster_ctas", C.c_int), ("grid_ctas", C.c_int), ("grid_threshold", C.c_int),
+        ("spin_limit", C.c_longlong), ("profile", C.c_int),
     ]
 
 
@@ -62,7 +63,8 @@ class PlanInfo(C.Structure):
 
 class Counters(C.Structure):
     _fields_ = [("krylov_iters", C.c_longlong), ("applies", C.c_longlong), ("contraction_flops", C.c_double),
-                ("not_converged", C.c_longlong), ("steps", C.c_longlong)]
+                ("not_converged", C.c_longlong), ("steps", C.c_longlong), ("op_seconds", (C.c_double * 2) * 6),
+                ("op_count", (C.c_longlong * 2) * 6)]
 
 
 _lib = None
@@ -94,6 +96,7 @@ def lib():
         L.ttns_free.argtypes = [C.c_void_p]
         L.ttns_free.restype = None
         L.ttns_plan.argtypes = [C.c_int, C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(PlanInfo)]
+        L.ttns_selftest_wait_timeout.argtypes = [C.c_longlong, C.POINTER(C.c_int)]
         L.ttns_chain_ohmic.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp, dp]
         L.ttns_chain_from_modes.argtypes = [C.c_int, dp, dp, C.c_int, dp, dp, dp]
         _lib = L
@@ -107,6 +110,12 @@ def _check(code: int) -> None:
 
 def _dptr(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def selftest_wait_timeout(spin_limit: int) -> int:
+    st = C.c_int(-1)
+    _check(lib().ttns_selftest_wait_timeout(spin_limit, C.byref(st)))
+    return st.value
 
 
 def chain_ohmic(alpha: float, omega_c: float, L: int):
@@ -171,7 +180,7 @@ def current_stream() -> Optional[int]:
 
 
 def _options(p0, precision, record=False, max_record=0, stream=None, cluster_ctas=0, grid_ctas=0,
-             krylov_tol=0.0, krylov_mmax=0, keep=None):
+             krylov_tol=0.0, krylov_mmax=0, keep=None, grid_threshold=0, spin_limit=0, profile=0):
     psi = None
     if p0.psi_el is not None:
         arr = _cplx(p0.psi_el)
@@ -179,7 +188,8 @@ def _options(p0, precision, record=False, max_record=0, stream=None, cluster_cta
             keep.append(arr)
         psi = _dptr(arr)
     return Options(precision, krylov_tol, krylov_mmax, stream, int(p0.er_tree), int(p0.D_er),
-                   int(p0.init_state), psi, int(record), int(max_record), cluster_ctas, grid_ctas)
+                   int(p0.init_state), psi, int(record), int(max_record), cluster_ctas, grid_ctas,
+                   grid_threshold, spin_limit, profile)
 
 
 def plan(problems, precision: int = TTNS_MIXED, krylov_mmax: int = 0) -> dict:
@@ -204,20 +214,18 @@ class Tree:
 
     def __init__(self, problems, precision: int = TTNS_MIXED, record: bool = False, max_record: int = 0,
                  stream: Optional[int] = None, cluster_ctas: int = 0, grid_ctas: int = 0,
-                 krylov_tol: float = 0.0, krylov_mmax: int = 0):
+                 krylov_tol: float = 0.0, krylov_mmax: int = 0, grid_threshold: int = 0, spin_limit: int = 0,
+                 profile: bool = False):
         single = not isinstance(problems, (list, tuple))
         probs = [problems] if single else list(problems)
         self.problems = probs
-        p0 = probs[0]
         self._keep = [_ProblemKeep(p) for p in probs]
-        psi = None
-        if p0.psi_el is not None:
-            self._psi = _cplx(p0.psi_el)
-            psi = _dptr(self._psi)
+        self._hold = []
         if stream is None:
             stream = current_stream()
-        self.opt = Options(precision, krylov_tol, krylov_mmax, stream, int(p0.er_tree), int(p0.D_er),
-                           int(p0.init_state), psi, int(record), int(max_record), cluster_ctas, grid_ctas)
+        self.opt = _options(probs[0], precision, record, max_record, stream, cluster_ctas, grid_ctas, krylov_tol,
+                            krylov_mmax, keep=self._hold, grid_threshold=grid_threshold, spin_limit=spin_limit,
+                            profile=int(profile))
         h = C.c_void_p()
         arr = (ProblemC * len(probs))(*[k.c for k in self._keep])
         if len(probs) == 1:
@@ -278,8 +286,14 @@ class Tree:
     def counters(self) -> dict:
         c = Counters()
         _check(lib().ttns_get_counters(self.h, C.byref(c)))
+        names = ["fwd", "qr", "env", "bond", "absorb", "record"]
+        prof = {}
+        for op in range(6):
+            for k, team in enumerate(["grid", "cluster"]):
+                if c.op_count[op][k]:
+                    prof[f"{names[op]}_{team}"] = (c.op_seconds[op][k], c.op_count[op][k])
         return {"krylov_iters": c.krylov_iters, "applies": c.applies, "contraction_flops": c.contraction_flops,
-                "not_converged": c.not_converged, "steps": c.steps}
+                "not_converged": c.not_converged, "steps": c.steps, "profile": prof}
 
     def n_nodes(self, k: int = 0) -> int:
         n = C.c_int()

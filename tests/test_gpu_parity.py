@@ -1,0 +1,258 @@
+"""GPU parity of the CUDA sweep with the FP64 CPU oracle, through the C ABI.
+
+Expected values come from the oracle: stored trajectories in tests/golden/
+(written by tests/golden/make_golden.py, which calls only oracle/), or an oracle
+run inside the test, or closed forms that do not depend on the oracle.
+
+Tolerances (populations, absolute):
+  FP64 path   1e-9   (both sides FP64; differences are rounding order and
+                      Krylov stopping points, both below 1e-12 per exponential)
+  mixed path  1e-6   (contractions in FP32-class arithmetic; the stated target)
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1710_01362_gb300 import build, ttns
+from paper_1710_01362_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+TOL = {ttns.TTNS_FP64: 1e-9, ttns.TTNS_MIXED: 1e-6}
+PRECS = [ttns.TTNS_FP64, ttns.TTNS_MIXED]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def golden(name):
+    path = os.path.join(GOLD, name + ".json")
+    if not os.path.exists(path):
+        pytest.skip(f"golden trajectory {name} not generated")
+    with open(path) as f:
+        return json.load(f)
+
+
+CASES = {
+    "ohmic_2state_L4_D4": lambda: W.ohmic_2state_L4(False),
+    "ohmic_2state_L4_fullD": lambda: W.ohmic_2state_L4(True),
+    "sf_small_s7": lambda: W.sf_small(seed=7, n_env=3, L=5, d=4, D=6, n_modes=12, n_steps=60),
+    "sf_small_er_s9": lambda: W.sf_small(seed=9, n_env=4, L=3, d=3, D=5, n_modes=6, n_steps=30, er_tree=True,
+                                         D_er=7),
+}
+
+
+def run_traj(p, n, prec, **kw):
+    g = ttns.Tree(p, precision=prec, record=True, max_record=max(n, 1), **kw)
+    g.step(p.dt, n)
+    tr = g.trajectory()
+    pops = np.real(np.einsum("kii->ki", tr))
+    return g, pops
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(CASES))
+def test_trajectory_matches_oracle(name, prec):
+    gd = golden(name)
+    p = CASES[name]()
+    n = gd["n_steps"]
+    g, pops = run_traj(p, n, prec)
+    ref = np.array(gd["populations"])[1:]
+    assert pops.shape == ref.shape
+    err = np.abs(pops - ref).max()
+    assert err < TOL[prec], f"max population error {err:.3e}"
+    occ = g.occupations()
+    np.testing.assert_allclose(occ, gd["occupations"][str(n)], atol=10 * TOL[prec])
+    nrm, en = g.observables()
+    assert abs(nrm - gd["norm"]) < 10 * TOL[prec]
+    assert abs(en - gd["energy"]) < 1e3 * TOL[prec]
+    g.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grid_team_path_matches_oracle(prec):
+    # every node handled by the whole-grid team (software barrier) instead of one cluster
+    gd = golden("sf_small_s7")
+    p = CASES["sf_small_s7"]()
+    g, pops = run_traj(p, 20, prec, grid_threshold=1)
+    ref = np.array(gd["populations"])[1:21]
+    assert np.abs(pops - ref).max() < TOL[prec]
+    g.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batched_trees_match_oracle(prec):
+    names = [f"batched_spin_boson_{s}" for s in range(1000, 1004)]
+    gds = [golden(n) for n in names]
+    ps = [W.batched_spin_boson(s) for s in range(1000, 1004)]
+    n = gds[0]["n_steps"]
+    g = ttns.Tree(ps, precision=prec, record=True, max_record=n)
+    g.step(ps[0].dt, n)
+    for k, gd in enumerate(gds):
+        tr = g.trajectory(k)
+        pops = np.real(np.einsum("kii->ki", tr))
+        ref = np.array(gd["populations"])[1:]
+        assert np.abs(pops - ref).max() < TOL[prec], names[k]
+    g.close()
+
+
+def test_batched_with_many_trees_equals_single_runs():
+    # 40 uneven trees in one persistent launch (more trees than clusters): each equals its
+    # own single-tree run bit for bit in the FP64 path (same arithmetic, same order)
+    ps = [W.batched_spin_boson(s, L=6 + s % 7, D=4 + s % 5) for s in range(40)]
+    g = ttns.Tree(ps, precision=ttns.TTNS_FP64)
+    g.step(0.5, 4)
+    for k in (0, 17, 39):
+        s = ttns.Tree(ps[k], precision=ttns.TTNS_FP64)
+        s.step(0.5, 4)
+        np.testing.assert_allclose(g.populations(k), s.populations(), atol=1e-13)
+        s.close()
+    g.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_singlet_fission_4x20_full_trajectory(prec):
+    """The headline workload at full size: 5 states, 4 chains x 20 sites, d 10, D 20,
+    400 steps of 0.5 fs, every population compared with the oracle's trajectory."""
+    gd = golden("sf_5state_4x20_d10_D20")
+    p = W.sf_5state_4x20()
+    n = gd["n_steps"]
+    g, pops = run_traj(p, n, prec)
+    ref = np.array(gd["populations"])[1:]
+    err = np.abs(pops - ref).max()
+    assert err < TOL[prec], f"max population error {err:.3e}"
+    occ = g.occupations()
+    assert np.abs(occ - np.array(gd["occupations"][str(n)])).max() < 10 * TOL[prec]
+    g.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_er_tree_8x12_reduced_length(prec):
+    """The ER-tree workload (5 states, 7 ER nodes, 8 chains, d 20, D 40) at reduced chain length 12."""
+    gd = golden("sf_er_5state_8x12_d20_D40")
+    p = W.sf_er_5state_8x60(L=12, n_steps=40)
+    n = gd["n_steps"]
+    g, pops = run_traj(p, n, prec)
+    ref = np.array(gd["populations"])[1:]
+    assert np.abs(pops - ref).max() < TOL[prec]
+    g.close()
+
+
+def test_initial_state_is_the_isometric_vacuum():
+    from oracle.model import build_tree, initial_tensors
+    p = W.sf_small(seed=7)
+    g = ttns.Tree(p, precision=ttns.TTNS_FP64)
+    A = initial_tensors(build_tree(p))
+    for v in range(g.n_nodes()):
+        assert np.array_equal(g.node(v), A[v])
+    assert np.allclose(g.populations(), [1, 0, 0, 0, 0][: p.n_el])
+    assert np.all(g.occupations() == 0)
+    g.close()
+
+
+def test_full_bond_dimension_equals_exact_state_vector():
+    from oracle.statevector import Exact
+    p = W.ohmic_2state_L4(True)
+    ex = Exact(p)
+    g, pops = run_traj(p, 100, ttns.TTNS_FP64)
+    ref = np.array([np.real(np.diag(ex.rho_el(ex.state((k + 1) * p.dt)))) for k in range(100)])
+    assert np.abs(pops - ref).max() < 5e-9
+    g.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_zero_coupling_rabi_formula(prec):
+    p = W.rabi(eps=0.1, V=0.05, n_steps=60)
+    g, pops = run_traj(p, 60, prec)
+    t = p.dt * np.arange(1, 61)
+    Om = np.sqrt(0.1 ** 2 + 0.05 ** 2)
+    P0 = 1.0 - (0.05 / Om) ** 2 * np.sin(Om * t / 0.6582119569) ** 2
+    assert np.abs(pops[:, 0] - P0).max() < (1e-10 if prec == ttns.TTNS_FP64 else 1e-6)
+    g.close()
+
+
+def test_pure_dephasing_closed_form():
+    from oracle.chain import chain_of
+    p = W.pure_dephasing()
+    n = p.n_steps
+    g = ttns.Tree(p, precision=ttns.TTNS_FP64, record=True, max_record=n)
+    g.step(p.dt, n)
+    tr = g.trajectory()
+    env = p.envs[0]
+    kappa = np.real(np.diag(env.W_bar))
+    eps = np.real(np.diag(p.H_S))
+    w, lam = env.spectral[1], env.spectral[2]
+    a = kappa[:, None] * lam[None, :] / (np.sqrt(2.0) * w[None, :])
+    for k in range(n):
+        t = (k + 1) * p.dt
+        x = w * t / 0.6582119569
+        expo = 1j * (a[0] ** 2 - a[1] ** 2) * (x - np.sin(x)) - (a[0] - a[1]) ** 2 * (1 - np.cos(x))
+        rho12 = 0.5 * np.exp(-1j * (eps[0] - eps[1]) * t / 0.6582119569) * np.exp(expo.sum())
+        assert abs(tr[k, 0, 1] - rho12) < 1e-8
+    g.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_norm_energy_and_density_matrix_properties(prec):
+    p = W.sf_small(seed=7)
+    g = ttns.Tree(p, precision=prec)
+    n0, e0 = g.observables()
+    g.step(p.dt, 40)
+    n1, e1 = g.observables()
+    tol = 1e-9 if prec == ttns.TTNS_FP64 else 1e-5
+    assert abs(n1 - 1.0) < tol and abs(e1 - e0) < tol
+    rho = g.rho()
+    assert np.abs(rho - rho.conj().T).max() < 1e-14
+    assert abs(np.trace(rho) - 1) < tol
+    assert np.linalg.eigvalsh(rho).min() > -1e-12
+    g.close()
+
+
+def test_checkpoint_resume_is_bitwise(tmp_path):
+    p = W.sf_small(seed=7)
+    a = ttns.Tree(p, precision=ttns.TTNS_MIXED)
+    a.step(p.dt, 6)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.step(p.dt, 6)
+    ra = a.rho()
+    b = ttns.Tree(p, precision=ttns.TTNS_MIXED)
+    b.load_state(path)
+    b.step(p.dt, 6)
+    rb = b.rho()
+    assert np.array_equal(ra, rb)
+    with open(path, "r+b") as f:
+        f.truncate(100)
+    with pytest.raises(ttns.TTNSError) as e:
+        b.load_state(path)
+    assert e.value.code == 7
+    a.close()
+    b.close()
+
+
+def test_repeated_runs_are_deterministic():
+    p = W.sf_small(seed=7)
+    r = []
+    for _ in range(2):
+        g = ttns.Tree(p, precision=ttns.TTNS_MIXED, grid_threshold=1)
+        g.step(p.dt, 5)
+        r.append(g.rho())
+        g.close()
+    assert np.array_equal(r[0], r[1])
+
+
+def test_bounded_wait_reports_timeout():
+    # a grid barrier that one CTA never reaches (a flag nothing sets): the waiting CTA gives
+    # up after the bound, the status word reads TTNS_E_TIMEOUT and the context stays usable
+    assert ttns.selftest_wait_timeout(200_000) == 5
+    assert ttns.selftest_wait_timeout(0) == 0   # both CTAs arrive: no timeout
+    p = W.sf_small(seed=7)
+    h = ttns.Tree(p, precision=ttns.TTNS_FP64)
+    h.step(p.dt, 1)
+    h.sync()
+    h.close()

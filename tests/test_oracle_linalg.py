@@ -87,3 +87,18 @@ def test_lanczos_invariant_subspace_is_exact():
     ref = np.exp(-3.0j * np.diag(H)) * v
     np.testing.assert_allclose(y, ref, atol=1e-13)
     assert stats["krylov_iters"] <= 4
+
+
+def test_lanczos_substeps_when_the_space_is_too_small():
+    # a wide spectrum and a long time: 10 Krylov vectors cannot reach 1e-12 in one go,
+    # the step is split and the result still matches expm
+    rng = np.random.default_rng(4)
+    n = 200
+    X = _rand(rng, n, n)
+    H = 2.0 * (X + X.conj().T) / np.sqrt(n)
+    v = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ref = scipy.linalg.expm(-1j * 1.0 * H) @ v
+    stats = {}
+    y = expm_lanczos(lambda x: H @ x, v, 1.0, mmax=10, stats=stats)
+    assert stats.get("substeps", 0) > 0 and stats.get("not_converged", 0) == 0
+    assert np.linalg.norm(y - ref) <= 1e-9 * np.linalg.norm(v)
