@@ -172,6 +172,13 @@ typedef struct {
    * (0 whole grid, 1 cluster), in seconds at the SM clock rate, and op counts */
   double op_seconds[6][2];
   long long op_count[6][2];
+  /* phases of the cluster-team Krylov exponentials: 0 operator staging, 1 first
+   * factors of two-factor terms, 2 apply + alpha reduction, 3 recurrence + beta
+   * reduction, 4 small exponential / convergence, 5 final combination, 6 norm */
+  double expm_phase_seconds[8];
+  /* phases of the cluster-team QRs: 0 copy + norm, 1 column loop, 2 Gram of the
+   * reflectors, 3 T and Z, 4 Q and R written back */
+  double qr_phase_seconds[8];
 } ttns_counters;
 ttns_status ttns_get_counters(ttns_tree* tree, ttns_counters* out);
 

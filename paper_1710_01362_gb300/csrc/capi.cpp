@@ -180,6 +180,14 @@ static ttns_status check_tables(const Compiled& C, int mmax, long long kvec, lon
   auto check_factor = [&](const Factor& f, const NodeDesc& nd) {
     if (f.leg < 0 || f.leg >= nd.nl) return false;
     const long long D = nd.dims[f.leg];
+    if (f.nnz < 0 || f.nnz > TTNS_SPARSE_MAX) return false;
+    if (f.nnz > 0) {
+      if (!in_pool(f.sp, 2 * D * f.nnz)) return false;
+      for (long long e = 0; e < D * f.nnz; ++e) {
+        const double c = C.pool_init[f.sp + D * f.nnz + e].x;
+        if (!(c >= 0.0 && c < (double)D)) return false;  // column index in range
+      }
+    }
     return in_pool(f.mat, D * D);
   };
   for (const Instr& I : C.prog) {
@@ -194,10 +202,15 @@ static ttns_status check_tables(const Compiled& C, int mmax, long long kvec, lon
       if (L.first < 0 || L.first + L.count > (int)C.terms.size() || L.n2 > n_tmp || L.n2 > L.count ||
           L.count > TTNS_MAX_TERMS)
         return fail(TTNS_E_INVALID, "table: term range");
+      const int n1 = L.count - L.n2 - L.nd;
+      if (n1 < 0 || L.nd < 0) return fail(TTNS_E_INVALID, "table: term counts");
       for (int k = 0; k < L.count; ++k) {
         const Term& T = C.terms[L.first + k];
-        const bool two = k >= L.count - L.n2;
+        const bool two = k >= n1;
         if (T.nf != (two ? 2 : 1)) return fail(TTNS_E_INVALID, "table: term order");
+        const bool direct = k >= n1 && k < n1 + L.nd;
+        if (direct && (T.sparse_f < 0 || T.sparse_f > 1 || T.f[T.sparse_f].nnz <= 0))
+          return fail(TTNS_E_INVALID, "table: direct term without a sparse factor");
         for (int j = 0; j < T.nf; ++j)
           if (!check_factor(T.f[j], nd)) return fail(TTNS_E_INVALID, "table: factor");
       }
@@ -268,6 +281,9 @@ static ttns_status device_init(ttns_tree* t) {
   grid = std::min(grid, maxgrid);
   grid = (grid / t->cluster) * t->cluster;
   if (grid < t->cluster) grid = t->cluster;
+  bool any_grid = false;
+  for (const Instr& I : C.prog) any_grid = any_grid || I.team == TEAM_GRID;
+  if (!t->batched && !any_grid) grid = t->cluster;  // one cluster does everything
   t->grid = grid;
   const int n_clusters = grid / t->cluster;
   const int n_workers = t->batched ? n_clusters : 1;
@@ -615,6 +631,8 @@ extern "C" ttns_status ttns_get_counters(ttns_tree* t, ttns_counters* out) {
       out->op_seconds[op][k] = h.prof_cycles[op][k] / hz;
       out->op_count[op][k] = (long long)h.prof_count[op][k];
     }
+  for (int k = 0; k < 8; ++k) out->expm_phase_seconds[k] = h.phase_cycles[k] / hz;
+  for (int k = 0; k < 8; ++k) out->qr_phase_seconds[k] = h.phase_cycles[8 + k] / hz;
   return TTNS_OK;
 }
 

@@ -36,21 +36,30 @@ struct NodeDesc {
   long long off;                 // offset of the tensor in the complex pool
 };
 
+#define TTNS_SPARSE_MAX 4  // nonzeros per row of a constant operator stored in row-sparse form
+
 struct Factor {
   int leg;        // leg of the tensor the matrix acts on
   long long mat;  // offset of a dims[leg] x dims[leg] row-major matrix in the complex pool
+  int nnz;        // 0: dense; else row-sparse with nnz entries per row (constant operators only)
+  long long sp;   // row-sparse table: dims*nnz values, then dims*nnz column indices (in .x)
 };
 
 struct Term {
   int nf;         // 1 or 2 factors
   Factor f[2];
+  int sparse_f;   // two-factor terms evaluated directly: index of the sparse factor
 };
 
-// A list of terms in the global term table.
+// A list of terms in the global term table, ordered
+//   [one-factor terms][direct two-factor terms][two-stage two-factor terms]
+// Direct terms (one factor row-sparse) are evaluated in one pass from the input;
+// two-stage terms go through a temporary (first factor, barrier, second factor).
 struct TermList {
   int first;
   int count;
-  int n2;         // number of two-factor terms (they come after the one-factor ones)
+  int n2;         // two-stage two-factor terms (the last n2 entries)
+  int nd;         // direct two-factor terms (before the two-stage ones)
 };
 
 struct Instr {
@@ -102,6 +111,9 @@ struct Ctl {
   int err_node;
   unsigned long long prof_cycles[8][2];  // per op code and team kind (rank-0 CTA clock cycles)
   unsigned long long prof_count[8][2];
+  unsigned long long phase_cycles[16];   // phases of the Krylov exponential (0-7) and QR (8-15), cluster team
+  unsigned progress;                     // bumped after every cluster-team instruction
+  unsigned pad1;
 };
 
 struct KernelParams {

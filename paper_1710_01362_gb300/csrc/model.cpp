@@ -238,6 +238,7 @@ struct TreeCompiler {
   std::vector<std::vector<char>> sub;   // subtree membership
   std::map<std::pair<int, int>, EnvInfo> env;
   std::vector<long long> opa_off, opb_off, onsite_off;
+  std::map<long long, std::pair<int, long long>> sparse_of;  // constant matrix offset -> (nnz, table offset)
   long long bond_off = 0;
   std::map<std::pair<int, int>, int> bond_node;   // (u, w) -> global pseudo-node id of bond X[i_u, i_w]
   std::map<std::pair<int, int>, int> bond_list;   // (u, w) -> term list index
@@ -255,6 +256,40 @@ struct TreeCompiler {
     long long off = (long long)C.pool_init.size();
     for (const cplx& z : m) C.pool_init.push_back(make_double2(z.real(), z.imag()));
     return off;
+  }
+  // constant operator: also store a row-sparse table when every row has few nonzeros
+  long long push_operator(const std::vector<cplx>& m) {
+    const long long off = push_matrix(m);
+    const int D = (int)std::lround(std::sqrt((double)m.size()));
+    int nnz = 0;
+    for (int i = 0; i < D; ++i) {
+      int c = 0;
+      for (int k = 0; k < D; ++k) c += std::abs(m[i * D + k]) > 0.0 ? 1 : 0;
+      nnz = std::max(nnz, c);
+    }
+    if (nnz >= 1 && nnz <= TTNS_SPARSE_MAX && nnz < D) {
+      const long long sp = (long long)C.pool_init.size();
+      C.pool_init.resize(C.pool_init.size() + 2LL * D * nnz, make_double2(0.0, 0.0));
+      for (int i = 0; i < D; ++i) {
+        int e = 0;
+        for (int k = 0; k < D; ++k) {
+          if (std::abs(m[i * D + k]) > 0.0) {
+            C.pool_init[sp + (long long)i * nnz + e] = make_double2(m[i * D + k].real(), m[i * D + k].imag());
+            C.pool_init[sp + (long long)D * nnz + (long long)i * nnz + e] = make_double2((double)k, 0.0);
+            ++e;
+          }
+        }
+      }
+      sparse_of[off] = {nnz, sp};
+    }
+    return off;
+  }
+  Factor with_sparse(Factor f) const {
+    f.nnz = 0;
+    f.sp = 0;
+    auto it = sparse_of.find(f.mat);
+    if (it != sparse_of.end()) { f.nnz = it->second.first; f.sp = it->second.second; }
+    return f;
   }
   long long push_zeros(long long n) {
     long long off = (long long)C.pool_init.size();
@@ -274,35 +309,55 @@ struct TreeCompiler {
   // factor of coupling k's end e seen from node u
   Factor end_factor(int u, int k, int e) const {
     const Coupling& cp = t.coups[k];
-    if (e == u) return Factor{t.phys_leg(u), e == cp.va ? opa_off[k] : opb_off[k]};
+    if (e == u) return with_sparse(Factor{t.phys_leg(u), e == cp.va ? opa_off[k] : opb_off[k], 0, 0});
     int w = toward(u, e);
     const EnvInfo& E = env.at({w, u});
     int pos = (int)(std::find(E.chans.begin(), E.chans.end(), k) - E.chans.begin());
     if (pos >= (int)E.chans.size()) throw std::logic_error("channel not found");
-    return Factor{t.leg_of(u, w), E.off + (long long)(1 + pos) * E.D * E.D};
+    return Factor{t.leg_of(u, w), E.off + (long long)(1 + pos) * E.D * E.D, 0, 0};
   }
   int slot(int v, int x) const { return x == v ? -1 : toward(v, x); }
 
   // terms of node u restricted to all neighbours except `excl` (-1: none)
+  // A two-factor term is evaluated directly (one pass, no temporary) when one factor is
+  // row-sparse and the direct cost nnz * D_dense is at most twice the two-stage cost.
+  static int direct_factor(const Term& T, const NodeDesc& nd) {
+    for (int f = 0; f < 2; ++f) {
+      const Factor& s_ = T.f[f];
+      const Factor& d_ = T.f[1 - f];
+      if (s_.nnz > 0 && d_.nnz == 0) {
+        const int Dd = nd.dims[d_.leg], Ds = nd.dims[s_.leg];
+        if (s_.nnz * Dd <= 2 * (Dd + Ds)) return f;
+      }
+    }
+    return -1;
+  }
+
   int node_terms(int u, int excl) {
-    std::vector<Term> one, two;
-    if (!t.onsite[u].empty()) one.push_back(Term{1, {Factor{t.phys_leg(u), onsite_off[u]}, Factor{0, 0}}});
+    std::vector<Term> one, direct, two;
+    const NodeDesc& nd = C.nodes[node0 + u];
+    if (!t.onsite[u].empty())
+      one.push_back(Term{1, {with_sparse(Factor{t.phys_leg(u), onsite_off[u], 0, 0}), Factor{0, 0, 0, 0}}, -1});
     for (int w : t.neighbours(u)) {
       if (w == excl) continue;
       const EnvInfo& E = env.at({w, u});
-      one.push_back(Term{1, {Factor{t.leg_of(u, w), E.off}, Factor{0, 0}}});
+      one.push_back(Term{1, {Factor{t.leg_of(u, w), E.off, 0, 0}, Factor{0, 0, 0, 0}}, -1});
     }
     for (int k = 0; k < (int)t.coups.size(); ++k) {
       const Coupling& cp = t.coups[k];
       if (excl >= 0 && (!in_piece(u, excl, cp.va) || !in_piece(u, excl, cp.vb))) continue;
       if (slot(u, cp.va) == slot(u, cp.vb)) continue;
-      two.push_back(Term{2, {end_factor(u, k, cp.va), end_factor(u, k, cp.vb)}});
+      Term T{2, {end_factor(u, k, cp.va), end_factor(u, k, cp.vb)}, -1};
+      T.sparse_f = direct_factor(T, nd);
+      (T.sparse_f >= 0 ? direct : two).push_back(T);
     }
     TermList L;
     L.first = (int)C.terms.size();
-    L.count = (int)(one.size() + two.size());
+    L.count = (int)(one.size() + direct.size() + two.size());
     L.n2 = (int)two.size();
+    L.nd = (int)direct.size();
     for (auto& x : one) C.terms.push_back(x);
+    for (auto& x : direct) C.terms.push_back(x);
     for (auto& x : two) C.terms.push_back(x);
     C.max_tmp = std::max(C.max_tmp, L.n2);
     C.lists.push_back(L);
@@ -314,7 +369,7 @@ struct TreeCompiler {
     double f = 0;
     for (int k = 0; k < L.count; ++k) {
       const Term& T = C.terms[L.first + k];
-      for (int j = 0; j < T.nf; ++j) f += 8.0 * nd.size * nd.dims[T.f[j].leg];
+      for (int j = 0; j < T.nf; ++j) f += 8.0 * nd.size * (T.f[j].nnz > 0 ? T.f[j].nnz : nd.dims[T.f[j].leg]);
     }
     return f;
   }
@@ -364,10 +419,10 @@ struct TreeCompiler {
     // operators
     onsite_off.assign(n, -1);
     for (int v = 0; v < n; ++v)
-      if (!t.onsite[v].empty()) onsite_off[v] = push_matrix(t.onsite[v]);
+      if (!t.onsite[v].empty()) onsite_off[v] = push_operator(t.onsite[v]);
     for (const Coupling& cp : t.coups) {
-      opa_off.push_back(push_matrix(cp.opa));
-      opb_off.push_back(push_matrix(cp.opb));
+      opa_off.push_back(push_operator(cp.opa));
+      opb_off.push_back(push_operator(cp.opb));
     }
     // environment blocks for every directed edge
     for (int u = 0; u < n; ++u) {
@@ -510,19 +565,20 @@ struct TreeCompiler {
       const EnvInfo& Ew = env.at({w, u});
       TermList L;
       L.first = (int)C.terms.size();
-      C.terms.push_back(Term{1, {Factor{0, Eu.off}, Factor{0, 0}}});
-      C.terms.push_back(Term{1, {Factor{1, Ew.off}, Factor{0, 0}}});
+      C.terms.push_back(Term{1, {Factor{0, Eu.off, 0, 0}, Factor{0, 0, 0, 0}}, -1});
+      C.terms.push_back(Term{1, {Factor{1, Ew.off, 0, 0}, Factor{0, 0, 0, 0}}, -1});
       int n2 = 0;
       for (size_t a = 0; a < Eu.chans.size(); ++a) {
         int k = Eu.chans[a];
         size_t b = std::find(Ew.chans.begin(), Ew.chans.end(), k) - Ew.chans.begin();
         if (b >= Ew.chans.size()) throw std::logic_error("bond channel mismatch");
-        C.terms.push_back(Term{2, {Factor{0, Eu.off + (long long)(1 + a) * Eu.D * Eu.D},
-                                   Factor{1, Ew.off + (long long)(1 + b) * Ew.D * Ew.D}}});
+        C.terms.push_back(Term{2, {Factor{0, Eu.off + (long long)(1 + a) * Eu.D * Eu.D, 0, 0},
+                                   Factor{1, Ew.off + (long long)(1 + b) * Ew.D * Ew.D, 0, 0}}, -1});
         ++n2;
       }
       L.count = 2 + n2;
       L.n2 = n2;
+      L.nd = 0;
       C.max_tmp = std::max(C.max_tmp, n2);
       C.lists.push_back(L);
       li = (int)C.lists.size() - 1;

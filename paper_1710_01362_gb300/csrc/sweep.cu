@@ -112,14 +112,21 @@ __device__ void grid_sync(Ctl* ctl, long long spin_limit) {
       __threadfence();
       asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&ctl->bar_gen), "r"(g + 1) : "memory");
     } else {
+      // bounded wait; the bound applies to time without progress of the working cluster
       long long t0 = clock64();
+      unsigned seen = *(volatile unsigned*)&ctl->progress;
       while (ld_acquire(&ctl->bar_gen) == g) {
         if (ld_volatile_int(&ctl->status) != 0) break;
+        const unsigned pr = *(volatile unsigned*)&ctl->progress;
+        if (pr != seen) {
+          seen = pr;
+          t0 = clock64();
+        }
         if (clock64() - t0 > spin_limit) {
           set_status(ctl, ST_TIMEOUT, 100, -1);
           break;
         }
-        __nanosleep(64);
+        __nanosleep(128);
       }
     }
     __threadfence();
@@ -230,10 +237,12 @@ __device__ __forceinline__ typename C2<T>::t mode_dot(const MT* row, int D, cons
 
 // Operator matrices of one op, staged once in dynamic shared memory in the compute type.
 // slot[t][f] gives the shared offset of factor f of term t (-1: read from the pool).
+// Row-sparse constant operators are read from their tables in the pool (a few entries).
 extern __shared__ __align__(16) unsigned char dyn_smem[];
 struct StageTable {
   int slot[TTNS_MAX_TERMS][2];
   int chan[16];
+  int end;        // first free element (compute type) after the staged matrices
 };
 
 template <typename T>
@@ -249,17 +258,19 @@ __device__ void stage_matrices(const KernelParams& P, const NodeDesc& nd, const 
       const Term& T_ = P.terms[L.first + t];
       for (int f = 0; f < 2; ++f) {
         st.slot[t][f] = -1;
-        if (f < T_.nf) {
+        if (f < T_.nf && T_.f[f].nnz == 0) {
           const long long need = (long long)nd.dims[T_.f[f].leg] * nd.dims[T_.f[f].leg];
           if (off + need <= cap) { st.slot[t][f] = (int)off; off += need; }
         }
       }
     }
+    for (int b = 0; b < 16; ++b) st.chan[b] = -1;
     for (int b = 0; b < nchan && b < 16; ++b) {
-      st.chan[b] = -1;
+      if (chans[b].nnz != 0) continue;
       const long long need = (long long)nd.dims[chans[b].leg] * nd.dims[chans[b].leg];
       if (off + need <= cap) { st.chan[b] = (int)off; off += need; }
     }
+    st.end = (int)((off + 1) & ~1LL);
   }
   __syncthreads();
   for (int t = 0; t < L.count && t < TTNS_MAX_TERMS; ++t) {
@@ -282,11 +293,40 @@ __device__ void stage_matrices(const KernelParams& P, const NodeDesc& nd, const 
   __syncthreads();
 }
 
+// Input vector staged in shared memory (compute type) after the matrices, when it fits.
+template <typename T>
+__device__ typename C2<T>::t* vec_smem(const KernelParams& P, const StageTable& st, long long N) {
+  using V = typename C2<T>::t;
+  const long long cap = P.smem_bytes / (long long)sizeof(V);
+  if ((long long)st.end + N > cap) return nullptr;
+  return reinterpret_cast<V*>(dyn_smem) + st.end;
+}
+
+template <typename T>
+__device__ void stage_vector(typename C2<T>::t* dst, const double2* src, long long N) {
+  __syncthreads();
+  for (long long k = threadIdx.x; k < N; k += NT) dst[k] = cvt<T>(src[k]);
+  __syncthreads();
+}
+
+// One factor applied at output idx: sum_k M[i][k] x[idx + (k - i) * stride] along the factor's leg.
 template <typename T, typename XT>
 __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, const NodeDesc& nd, const Factor& f,
                                                         int slot, const XT* x, long long idx) {
   const LegPos lp = leg_pos(nd, f.leg, idx);
   const int D = nd.dims[f.leg];
+  if (f.nnz > 0) {
+    using V = typename C2<T>::t;
+    V acc;
+    acc.x = acc.y = (T)0;
+    const double2* vals = P.pool + f.sp + (long long)lp.i * f.nnz;
+    const double2* cols = P.pool + f.sp + (long long)D * f.nnz + (long long)lp.i * f.nnz;
+    for (int e = 0; e < f.nnz; ++e) {
+      const int k = (int)cols[e].x;
+      cmac<T>(acc, cvt<T>(vals[e]), cvt<T>(x[lp.base + (long long)k * nd.strides[f.leg]]));
+    }
+    return acc;
+  }
   if (slot >= 0) {
     const typename C2<T>::t* sm = reinterpret_cast<const typename C2<T>::t*>(dyn_smem) + slot;
     return mode_dot<T>(sm + lp.i * D, D, x, lp.base, nd.strides[f.leg]);
@@ -294,38 +334,71 @@ __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, c
   return mode_dot<T>(P.pool + f.mat + (long long)lp.i * D, D, x, lp.base, nd.strides[f.leg]);
 }
 
-// Stage 1: tmp[t] = first factor of two-factor term t applied to x (tmp in the compute type)
-template <typename T>
-__device__ void apply_stage1(const KernelParams& P, Team& tm, const NodeDesc& nd, const double2* x, const TermList& L,
+// Direct two-factor term at idx: the sparse factor's few entries, each times the dense
+// factor applied at the shifted position.
+template <typename T, typename XT>
+__device__ __forceinline__ typename C2<T>::t direct_dot(const KernelParams& P, const NodeDesc& nd, const Term& T_,
+                                                        int dense_slot, const XT* x, long long idx) {
+  using V = typename C2<T>::t;
+  const Factor& sf = T_.f[T_.sparse_f];
+  const Factor& df = T_.f[1 - T_.sparse_f];
+  const LegPos lp = leg_pos(nd, sf.leg, idx);
+  const int Ds = nd.dims[sf.leg];
+  const double2* vals = P.pool + sf.sp + (long long)lp.i * sf.nnz;
+  const double2* cols = P.pool + sf.sp + (long long)Ds * sf.nnz + (long long)lp.i * sf.nnz;
+  V acc;
+  acc.x = acc.y = (T)0;
+  for (int e = 0; e < sf.nnz; ++e) {
+    const double2 v = vals[e];
+    if (v.x == 0.0 && v.y == 0.0) continue;
+    const long long idx2 = lp.base + (long long)((int)cols[e].x) * nd.strides[sf.leg];
+    const V d = factor_dot<T>(P, nd, df, dense_slot, x, idx2);
+    cmac<T>(acc, cvt<T>(v), d);
+  }
+  return acc;
+}
+
+// Stage 1: tmp[t] = first factor of two-stage term t applied to x (tmp in the compute type)
+template <typename T, typename XT>
+__device__ void apply_stage1(const KernelParams& P, Team& tm, const NodeDesc& nd, const XT* x, const TermList& L,
                              typename C2<T>::t* tmp, long long tstride, const StageTable& st) {
-  const int n1 = L.count - L.n2;
-  const Term* terms = P.terms + L.first + n1;
+  const int t0 = L.count - L.n2;
+  const Term* terms = P.terms + L.first + t0;
   const long long N = nd.size;
   for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
     for (int t = 0; t < L.n2; ++t) {
-      tmp[t * tstride + idx] = factor_dot<T>(P, nd, terms[t].f[0], n1 + t < TTNS_MAX_TERMS ? st.slot[n1 + t][0] : -1, x, idx);
+      const int tt = t0 + t;
+      tmp[t * tstride + idx] = factor_dot<T>(P, nd, terms[t].f[0], tt < TTNS_MAX_TERMS ? st.slot[tt][0] : -1, x, idx);
     }
   }
 }
 
-// Stage 2 value at idx: one-factor terms on x plus second factors on tmp
-template <typename T>
-__device__ __forceinline__ typename C2<T>::t apply_stage2_at(const KernelParams& P, const NodeDesc& nd, const double2* x,
+// Stage 2 value at idx: one-factor and direct terms on x, second factors on tmp
+template <typename T, typename XT>
+__device__ __forceinline__ typename C2<T>::t apply_stage2_at(const KernelParams& P, const NodeDesc& nd, const XT* x,
                                                             const TermList& L, const typename C2<T>::t* tmp,
                                                             long long tstride, long long idx, const StageTable& st) {
   typename C2<T>::t acc;
   acc.x = 0;
   acc.y = 0;
   const Term* terms = P.terms + L.first;
-  const int n1 = L.count - L.n2;
+  const int n1 = L.count - L.n2 - L.nd;
   for (int t = 0; t < n1; ++t) {
     const auto a = factor_dot<T>(P, nd, terms[t].f[0], t < TTNS_MAX_TERMS ? st.slot[t][0] : -1, x, idx);
     acc.x += a.x;
     acc.y += a.y;
   }
+  for (int t = n1; t < n1 + L.nd; ++t) {
+    const int ds = t < TTNS_MAX_TERMS ? st.slot[t][1 - terms[t].sparse_f] : -1;
+    const auto a = direct_dot<T>(P, nd, terms[t], ds, x, idx);
+    acc.x += a.x;
+    acc.y += a.y;
+  }
+  const int t0 = L.count - L.n2;
   for (int t = 0; t < L.n2; ++t) {
-    const auto a = factor_dot<T>(P, nd, terms[n1 + t].f[1], n1 + t < TTNS_MAX_TERMS ? st.slot[n1 + t][1] : -1,
-                                 tmp + t * tstride, idx);
+    const int tt = t0 + t;
+    const auto a = factor_dot<T>(P, nd, terms[tt].f[1], tt < TTNS_MAX_TERMS ? st.slot[tt][1] : -1, tmp + t * tstride,
+                                 idx);
     acc.x += a.x;
     acc.y += a.y;
   }
@@ -363,16 +436,25 @@ __device__ void texp_warp(const double* a, const double* b, int m, double s, dou
     if (nsub < 1) nsub = 1;
     const double z = s * R / nsub;     // signed
     const double az = fabs(z);
-    int K = (int)ceil(1.2 * az + 18.0);
-    if (K > 64) K = 64;
+    // truncation: the last coefficient ~ 2 (|z|/2)^K / K! below 1e-17
+    int K = 1;
+    {
+      double term = 1.0;
+      while (K < 64 && (term > 1e-18 || K < (int)az + 2)) {
+        term *= 0.5 * az * c_inv[K];
+        ++K;
+      }
+    }
     // Bessel J_n(|z|) for n = lane and lane + 32 via the power series in Horner form
     double J[2];
     const double y = -0.25 * az * az;
+    int jmax = (int)(3.0 * az + 8.0);
+    if (jmax > 24) jmax = 24;
     for (int h = 0; h < 2; ++h) {
       const int n = lane + 32 * h;
       double acc = 1.0;
       if (n < K) {
-        for (int j = 24; j >= 1; --j) acc = fma(acc * y, c_inv[j] * c_inv[j + n], 1.0);
+        for (int j = jmax; j >= 1; --j) acc = fma(acc * y, c_inv[j] * c_inv[j + n], 1.0);
         J[h] = acc * pow(0.5 * az, (double)n) * c_invfact[n];
       } else {
         J[h] = 0.0;
@@ -436,9 +518,26 @@ struct KrylovShared {
   int flag;
 };
 
+struct PhaseClock {
+  long long t;
+  bool on;
+  __device__ void start(bool enable) {
+    on = enable;
+    t = clock64();
+  }
+  __device__ void lap(Ctl* ctl, int phase) {
+    if (!on) return;
+    const long long now = clock64();
+    atomicAdd(&ctl->phase_cycles[phase], (unsigned long long)(now - t));
+    t = now;
+  }
+};
+
 template <typename T>
 __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2* work, double tau) {
   __shared__ KrylovShared ks;
+  PhaseClock pc;
+  pc.start(P.profile && tm.kind == TEAM_CLUSTER && tm.rank == 0 && threadIdx.x == 0);
   const NodeDesc nd = P.nodes[I.node];
   const TermList L = P.lists[I.terms];
   const long long N = nd.size;
@@ -450,6 +549,8 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
   const int mmax = min(P.mmax, (int)(N < (long long)TTNS_KMAX ? N : (long long)TTNS_KMAX));
   __shared__ StageTable st;
   stage_matrices<T>(P, nd, L, nullptr, 0, st);
+  typename C2<T>::t* xs = vec_smem<T>(P, st, N);  // input vector in shared memory when it fits
+  pc.lap(P.ctl, 0);
   // exp(-i s H): s = time / hbar with the op's sign.  If the Krylov space of dimension
   // mmax does not reach the tolerance for the remaining time, the largest s / 2^k that
   // does is taken on the same space and a new space is built for the rest.
@@ -465,6 +566,7 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
     }
     team_allreduce(tm, v, 1);
     const double beta0 = sqrt(v[0]);
+    pc.lap(P.ctl, 6);
     if (!(beta0 > 0.0)) {
       if (!(beta0 == 0.0)) set_status(P.ctl, ST_NONFINITE, I.op, I.node);
       break;
@@ -474,11 +576,13 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
       ks.beta[0] = 0.0;
     }
     __syncthreads();
-    int hint = P.mhist[I.hist];
-    if (hint < 2) hint = 2;
     m = 0;
     bool conv = false;
     double bnext = 0.0;
+    // leading-order size of |e_m^T exp(-i s T_m) e_0|: |s|^(m-1) prod beta_i / (m-1)!,
+    // used to decide when the exact (small-exponential) check is worth running
+    double lead = 1.0;
+    int next_check = 1;
     for (int j = 0; j < mmax; ++j) {
       double2* Kj = Kp(j);
       double2* Kjm = j > 0 ? Kp(j - 1) : x;
@@ -486,13 +590,19 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
       const double sj = ks.scale[j];
       const double bj = ks.beta[j];
       const double sjm = j > 0 ? ks.scale[j - 1] : 0.0;
+      if (xs) stage_vector<T>(xs, Kj, N);
       if (L.n2 > 0) {
-        apply_stage1<T>(P, tm, nd, Kj, L, tmp, kv, st);
+        if (xs)
+          apply_stage1<T>(P, tm, nd, xs, L, tmp, kv, st);
+        else
+          apply_stage1<T>(P, tm, nd, Kj, L, tmp, kv, st);
         team_sync(tm);
       }
+      pc.lap(P.ctl, 1);
       double part[1] = {0.0};
       for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-        const auto a = apply_stage2_at<T>(P, nd, Kj, L, tmp, kv, idx, st);
+        const auto a = xs ? apply_stage2_at<T>(P, nd, xs, L, tmp, kv, idx, st)
+                          : apply_stage2_at<T>(P, nd, Kj, L, tmp, kv, idx, st);
         const double2 kj = Kj[idx];
         double wr = sj * (double)a.x, wi = sj * (double)a.y;
         if (j > 0) {
@@ -504,6 +614,7 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
         part[0] = fma(kj.x, wr, fma(kj.y, wi, part[0]));  // Re(conj(K_j) w)
       }
       team_allreduce(tm, part, 1);
+      pc.lap(P.ctl, 2);
       const double aj = part[0] * sj;
       part[0] = 0.0;
       for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
@@ -516,6 +627,7 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
       }
       team_allreduce(tm, part, 1);
       bnext = sqrt(part[0]);
+      pc.lap(P.ctl, 3);
       if (threadIdx.x == 0) {
         ks.alpha[j] = aj;
         ks.beta[j + 1] = bnext;
@@ -523,7 +635,10 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
       }
       __syncthreads();
       m = j + 1;
-      if (m >= hint - 1 || m == mmax || !(bnext > 0.0)) {
+      const double est = bnext * lead;
+      lead *= fabs(s_rem) * bnext / (double)m;
+      if ((est <= 1e3 * P.tol && m >= next_check) || m == mmax || !(bnext > 0.0)) {
+        next_check = m + 2;
         if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s_rem, ks.ure, ks.uim);
         __syncthreads();
         const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);
@@ -534,6 +649,7 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
         } else if (err <= P.tol || !(bnext > 0.0)) {
           conv = true;
         }
+        pc.lap(P.ctl, 4);
         if (conv || m == mmax) break;
       }
     }
@@ -549,6 +665,7 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
         __syncthreads();
         if (bnext * um <= P.tol) break;
       }
+      pc.lap(P.ctl, 4);
     }
     // y = beta0 * sum_k u_k q_k written over x (each thread reads its own K_0 = x entries first)
     for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
@@ -563,6 +680,7 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
       x[idx] = make_double2(yr, yi);
     }
     team_sync(tm);
+    pc.lap(P.ctl, 5);
     if (conv || m >= N || s_done == s_rem) break;
     s_rem -= s_done;
     if (chunk == 63 && tm.rank == 0 && threadIdx.x == 0) atomicAdd(&P.ctl->not_converged, 1ull);
@@ -598,6 +716,8 @@ __device__ __forceinline__ long long qr_addr(const NodeDesc& nd, int l, long lon
 // The helpers below walk them in a fixed order.
 __device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
   __shared__ QRShared qs;
+  PhaseClock pc;
+  pc.start(P.profile && tm.kind == TEAM_CLUSTER && tm.rank == 0 && threadIdx.x == 0);
   const NodeDesc nd = P.nodes[I.node];
   const int l = I.leg;
   const int n = nd.dims[l];
@@ -624,6 +744,7 @@ __device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* 
     }
   }
   team_allreduce(tm, v, 4);
+  pc.lap(P.ctl, 8);
   const double thr = QR_NULL_REL * sqrt(v[0]);
   double sig2 = v[1];
   double2 x0 = make_double2(v[2], v[3]);
@@ -717,6 +838,7 @@ __device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* 
     }
   }
   __syncthreads();
+  pc.lap(P.ctl, 9);
   // Gram of the Householder vectors: G[a][b] = v_a^H v_b over rows r >= max(a, b)
   {
     double* part = team_partials(tm);
@@ -754,6 +876,7 @@ __device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* 
     tm.parity ^= 1;
     __syncthreads();
   }
+  pc.lap(P.ctl, 10);
   // T (upper triangular): T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j]
   for (int idx = threadIdx.x; idx < n * n; idx += NT) Tm[idx / n * TTNS_MAX_D + idx % n] = make_double2(0, 0);
   __syncthreads();
@@ -786,6 +909,7 @@ __device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* 
     }
     Z[j * TTNS_MAX_D + c] = make_double2(zr, zi);
   }
+  pc.lap(P.ctl, 11);
   // phases of the diagonal of R
   for (int j = threadIdx.x; j < n; j += NT) {
     const double2 a = qs.rdiag[j];
@@ -821,6 +945,7 @@ __device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* 
     }
   }
   team_sync(tm);
+  pc.lap(P.ctl, 12);
 }
 
 // ------------------------------------------------------------------ absorb
@@ -858,16 +983,22 @@ __device__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2*
   const int nb = 1 + I.nchan;
   __shared__ StageTable st;
   stage_matrices<T>(P, nd, L, P.chans + I.chan_first, I.nchan, st);
+  typename C2<T>::t* xs = vec_smem<T>(P, st, N);
+  if (xs) stage_vector<T>(xs, Q, N);
   if (L.n2 > 0) {
-    apply_stage1<T>(P, tm, nd, Q, L, tmp, kv, st);
+    if (xs)
+      apply_stage1<T>(P, tm, nd, xs, L, tmp, kv, st);
+    else
+      apply_stage1<T>(P, tm, nd, Q, L, tmp, kv, st);
     team_sync(tm);
   }
   for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-    auto a = apply_stage2_at<T>(P, nd, Q, L, tmp, kv, idx, st);
+    auto a = xs ? apply_stage2_at<T>(P, nd, xs, L, tmp, kv, idx, st) : apply_stage2_at<T>(P, nd, Q, L, tmp, kv, idx, st);
     Y[idx] = make_double2((double)a.x, (double)a.y);
     for (int b = 0; b < I.nchan; ++b) {
       const Factor f = P.chans[I.chan_first + b];
-      auto c = factor_dot<T>(P, nd, f, b < 16 ? st.chan[b] : -1, Q, idx);
+      auto c = xs ? factor_dot<T>(P, nd, f, b < 16 ? st.chan[b] : -1, xs, idx)
+                  : factor_dot<T>(P, nd, f, b < 16 ? st.chan[b] : -1, Q, idx);
       Y[(long long)(1 + b) * kv + idx] = make_double2((double)c.x, (double)c.y);
     }
   }
@@ -1039,6 +1170,7 @@ __device__ void run(const KernelParams& P, int phase) {
         exec<T>(P, gt, I, P.work);
       } else if (cluster_id == 0) {
         exec<T>(P, ct, I, cwork);
+        if (crank == 0 && threadIdx.x == 0) atomicAdd(&P.ctl->progress, 1u);
       }
       prev = I.team;
     }

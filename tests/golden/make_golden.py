@@ -36,11 +36,24 @@ CASES = {
 for s in range(1000, 1004):
     CASES[f"batched_spin_boson_{s}"] = ((lambda s=s: W.batched_spin_boson(s)), 60, 10)
 
+# Sensitivity envelopes: the same oracle with a tighter Krylov tolerance.  Where the
+# one-site TDVP trajectory is ill-conditioned (rank-deficient bonds whose completion
+# directions are set by tiny amplitudes), two correct runs drift apart; this run
+# measures by how much, for the parity tests' long-horizon bound.
+TIGHT = {f"batched_spin_boson_{s}_tol14": (f"batched_spin_boson_{s}", 1e-14) for s in range(1000, 1004)}
+TIGHT["sf_er_5state_8x12_d20_D40_tol14"] = ("sf_er_5state_8x12_d20_D40", 1e-14)
+TIGHT["sf_5state_4x20_d10_D20_tol14"] = ("sf_5state_4x20_d10_D20", 1e-14)
+
 
 def run_case(name: str) -> None:
-    factory, n_steps, occ_every = CASES[name]
+    tol = None
+    if name in TIGHT:
+        base, tol = TIGHT[name]
+        factory, n_steps, occ_every = CASES[base]
+    else:
+        factory, n_steps, occ_every = CASES[name]
     p = factory()
-    st = TTNS(p)
+    st = TTNS(p) if tol is None else TTNS(p, tol=tol)
     pops = [st.populations().tolist()]
     occ = {0: st.occupations().tolist()}
     t0 = time.time()
