@@ -199,6 +199,24 @@ ttns_status ttns_load_state(ttns_tree* tree, const char* path);
  * *device_status receives TTNS_OK.  Uses the legacy default stream. */
 ttns_status ttns_selftest_wait_timeout(long long spin_limit, int* device_status);
 
+/* Electronic reduced density matrix from a root tensor in caller-owned device
+ * memory, allocating nothing (the paper has no counterpart: this is for callers
+ * that cannot call cudaMalloc, e.g. code running inside another framework's
+ * locked memory pool or on threads that must not trigger an allocation).
+ *   d_root   device pointer: rows x n_el complex (interleaved doubles), row-major,
+ *            the electronic leg last (the root layout of ttns_get_node)
+ *   rows     product of the root's bond dimensions, >= 1
+ *   n_el     1..16 electronic states
+ *   d_rho    device pointer: n_el x n_el complex output, rho[s][s'] = sum_r A[r][s] conj(A[r][s'])
+ *   cuda_stream  stream the two kernels are enqueued on (NULL = legacy default stream)
+ * Partial sums go to a fixed 1 MiB scratch array owned by the library on every
+ * device that loads it; n_el > 16 is rejected with TTNS_E_INVALID.  The first call
+ * on a device looks up that array's address (with the device current): make it
+ * before any stream capture.  Calls share the array, so calls that overlap on the
+ * GPU race; each call overwrites all the partials it uses.  Asynchronous. */
+ttns_status ttns_rho_from_root_noalloc(const double* d_root, long long rows, int n_el, double* d_rho,
+                                       void* cuda_stream);
+
 const char* ttns_last_error(void);
 void ttns_free(ttns_tree* tree);
 

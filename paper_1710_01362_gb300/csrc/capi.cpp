@@ -27,6 +27,10 @@ using namespace ttns;
 
 static thread_local std::string g_err;
 
+namespace ttns {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace ttns
+
 static ttns_status fail(ttns_status st, const std::string& msg) {
   g_err = msg;
   return st;

@@ -25,6 +25,7 @@ EXPORTS = [
     "ttns_occupations", "ttns_observables", "ttns_trajectory", "ttns_populations_device", "ttns_get_counters",
     "ttns_node_info", "ttns_get_node", "ttns_save", "ttns_load_state", "ttns_last_error", "ttns_free",
     "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan", "ttns_selftest_wait_timeout",
+    "ttns_rho_from_root_noalloc",
 ]
 
 
@@ -98,6 +99,7 @@ def lib():
         L.ttns_free.restype = None
         L.ttns_plan.argtypes = [C.c_int, C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(PlanInfo)]
         L.ttns_selftest_wait_timeout.argtypes = [C.c_longlong, C.POINTER(C.c_int)]
+        L.ttns_rho_from_root_noalloc.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
         L.ttns_chain_ohmic.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp, dp]
         L.ttns_chain_from_modes.argtypes = [C.c_int, dp, dp, C.c_int, dp, dp, dp]
         _lib = L
@@ -117,6 +119,12 @@ def selftest_wait_timeout(spin_limit: int) -> int:
     st = C.c_int(-1)
     _check(lib().ttns_selftest_wait_timeout(spin_limit, C.byref(st)))
     return st.value
+
+
+def rho_from_root_noalloc(d_root: int, rows: int, n_el: int, d_rho: int, stream: Optional[int] = None) -> None:
+    """Allocation-free electronic density matrix from a root tensor in device memory
+    (device pointers given as integers); enqueued on `stream`."""
+    _check(lib().ttns_rho_from_root_noalloc(C.c_void_p(d_root), rows, n_el, C.c_void_p(d_rho), C.c_void_p(stream)))
 
 
 def chain_ohmic(alpha: float, omega_c: float, L: int):
