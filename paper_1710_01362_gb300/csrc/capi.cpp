@@ -278,7 +278,7 @@ static ttns_status device_init(ttns_tree* t) {
   t->cluster = o.cluster_ctas > 0 ? o.cluster_ctas : 16;
   if (t->cluster > 16) return fail(TTNS_E_INVALID, "cluster_ctas must be <= 16");
   int maxgrid = 0;
-  const long long smem_bytes = 160 * 1024;
+  const long long smem_bytes = 200 * 1024;
   CUDA_TRY(max_grid_for(t->cluster, smem_bytes, &maxgrid));
   if (maxgrid < t->cluster) return fail(TTNS_E_CUDA, "no co-resident cluster of the requested size");
   int grid = o.grid_ctas > 0 ? o.grid_ctas : maxgrid;
@@ -358,6 +358,7 @@ static ttns_status device_init(ttns_tree* t) {
   P.spin_limit = o.spin_limit > 0 ? o.spin_limit : 20LL * 1000 * 1000 * 1000;  // SM clock cycles (~10 s)
   P.profile = o.profile;
   P.smem_bytes = smem_bytes;
+  P.cluster_resident = 1;
   // initial environment pass
   CUDA_TRY(launch_sweep(P, 0, t->grid, t->cluster, t->stream));
   CUDA_TRY(cudaStreamSynchronize(t->stream));

@@ -34,6 +34,8 @@ struct NodeDesc {
   int strides[TTNS_MAX_LEGS];    // row-major strides
   int size;                      // product of dims
   long long off;                 // offset of the tensor in the complex pool
+  long long reg_off;             // operator region: the environment blocks flowing into this node
+  int reg_len;                   // and its constant operators, contiguous (staged together)
 };
 
 #define TTNS_SPARSE_MAX 4  // nonzeros per row of a constant operator stored in row-sparse form
@@ -77,6 +79,8 @@ struct Instr {
   int hist;        // Krylov-length history slot (FWD, BOND)
   double sign;     // FWD +1, BOND -1 (sign of the time argument)
   double flops;    // useful flops of one application of this op's operator
+  long long rega_off, regb_off;  // operator regions staged in shared memory for this op
+  int rega_len, regb_len;
 };
 
 // Per-tree description used by the device.
@@ -152,6 +156,7 @@ struct KernelParams {
   long long spin_limit;
   int profile;
   long long smem_bytes;    // dynamic shared memory per CTA (operator matrices of one op)
+  int cluster_resident;    // 1: small-node Krylov exponentials kept in the cluster's shared memory
 };
 
 }  // namespace ttns

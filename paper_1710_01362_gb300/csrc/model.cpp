@@ -257,32 +257,42 @@ struct TreeCompiler {
     for (const cplx& z : m) C.pool_init.push_back(make_double2(z.real(), z.imag()));
     return off;
   }
-  // constant operator: also store a row-sparse table when every row has few nonzeros
+  // constant operator: a dense matrix in the current region; when every row has few
+  // nonzeros, a row-sparse table is also built (placed after all regions, see finish_sparse)
+  std::vector<std::pair<long long, std::vector<cplx>>> pending_sparse;
   long long push_operator(const std::vector<cplx>& m) {
     const long long off = push_matrix(m);
-    const int D = (int)std::lround(std::sqrt((double)m.size()));
-    int nnz = 0;
-    for (int i = 0; i < D; ++i) {
-      int c = 0;
-      for (int k = 0; k < D; ++k) c += std::abs(m[i * D + k]) > 0.0 ? 1 : 0;
-      nnz = std::max(nnz, c);
-    }
-    if (nnz >= 1 && nnz <= TTNS_SPARSE_MAX && nnz < D) {
-      const long long sp = (long long)C.pool_init.size();
-      C.pool_init.resize(C.pool_init.size() + 2LL * D * nnz, make_double2(0.0, 0.0));
+    pending_sparse.push_back({off, m});
+    return off;
+  }
+  void finish_sparse() {
+    for (auto& pr : pending_sparse) {
+      const long long off = pr.first;
+      const std::vector<cplx>& m = pr.second;
+      const int D = (int)std::lround(std::sqrt((double)m.size()));
+      int nnz = 0;
       for (int i = 0; i < D; ++i) {
-        int e = 0;
-        for (int k = 0; k < D; ++k) {
-          if (std::abs(m[i * D + k]) > 0.0) {
-            C.pool_init[sp + (long long)i * nnz + e] = make_double2(m[i * D + k].real(), m[i * D + k].imag());
-            C.pool_init[sp + (long long)D * nnz + (long long)i * nnz + e] = make_double2((double)k, 0.0);
-            ++e;
+        int c = 0;
+        for (int k = 0; k < D; ++k) c += std::abs(m[i * D + k]) > 0.0 ? 1 : 0;
+        nnz = std::max(nnz, c);
+      }
+      if (nnz >= 1 && nnz <= TTNS_SPARSE_MAX && nnz < D) {
+        const long long sp = (long long)C.pool_init.size();
+        C.pool_init.resize(C.pool_init.size() + 2LL * D * nnz, make_double2(0.0, 0.0));
+        for (int i = 0; i < D; ++i) {
+          int e = 0;
+          for (int k = 0; k < D; ++k) {
+            if (std::abs(m[i * D + k]) > 0.0) {
+              C.pool_init[sp + (long long)i * nnz + e] = make_double2(m[i * D + k].real(), m[i * D + k].imag());
+              C.pool_init[sp + (long long)D * nnz + (long long)i * nnz + e] = make_double2((double)k, 0.0);
+              ++e;
+            }
           }
         }
+        sparse_of[off] = {nnz, sp};
       }
-      sparse_of[off] = {nnz, sp};
     }
-    return off;
+    pending_sparse.clear();
   }
   Factor with_sparse(Factor f) const {
     f.nnz = 0;
@@ -381,6 +391,8 @@ struct TreeCompiler {
     for (int k = d.nl - 1; k >= 0; --k) { d.dims[k] = dims[k]; d.strides[k] = s; s *= dims[k]; }
     d.size = s;
     d.off = off;
+    d.reg_off = 0;
+    d.reg_len = 0;
     return d;
   }
 
@@ -416,27 +428,33 @@ struct TreeCompiler {
       C.max_node = std::max<int>(C.max_node, (int)size);
       for (int x : dims) C.max_D = std::max(C.max_D, x);
     }
-    // operators
+    // operator regions: for every node v, the environment blocks flowing into v (one
+    // directed edge w -> v per neighbour) followed by v's constant operators, contiguous so
+    // that an op on v stages them with one copy
     onsite_off.assign(n, -1);
-    for (int v = 0; v < n; ++v)
-      if (!t.onsite[v].empty()) onsite_off[v] = push_operator(t.onsite[v]);
-    for (const Coupling& cp : t.coups) {
-      opa_off.push_back(push_operator(cp.opa));
-      opb_off.push_back(push_operator(cp.opb));
-    }
-    // environment blocks for every directed edge
-    for (int u = 0; u < n; ++u) {
-      for (int v : t.neighbours(u)) {
+    opa_off.assign(t.coups.size(), -1);
+    opb_off.assign(t.coups.size(), -1);
+    for (int v = 0; v < n; ++v) {
+      const long long reg0 = (long long)C.pool_init.size();
+      for (int w : t.neighbours(v)) {
         EnvInfo E;
-        E.D = (t.parent[u] == v) ? t.bond[u] : t.bond[v];
+        E.D = (t.parent[w] == v) ? t.bond[w] : t.bond[v];
         for (int k = 0; k < (int)t.coups.size(); ++k) {
-          bool a = in_piece(u, v, t.coups[k].va), b = in_piece(u, v, t.coups[k].vb);
+          bool a = in_piece(w, v, t.coups[k].va), b = in_piece(w, v, t.coups[k].vb);
           if (a != b) E.chans.push_back(k);
         }
         E.off = push_zeros((long long)(1 + E.chans.size()) * E.D * E.D);
-        env[{u, v}] = E;
+        env[{w, v}] = E;
       }
+      if (!t.onsite[v].empty()) onsite_off[v] = push_operator(t.onsite[v]);
+      for (int k = 0; k < (int)t.coups.size(); ++k) {
+        if (t.coups[k].va == v) opa_off[k] = push_operator(t.coups[k].opa);
+        if (t.coups[k].vb == v) opb_off[k] = push_operator(t.coups[k].opb);
+      }
+      C.nodes[node0 + v].reg_off = reg0;
+      C.nodes[node0 + v].reg_len = (int)((long long)C.pool_init.size() - reg0);
     }
+    finish_sparse();
     bond_off = push_zeros((long long)TTNS_MAX_D * TTNS_MAX_D);
     // pseudo nodes for bond matrices
     for (int u = 0; u < n; ++u)
@@ -444,6 +462,8 @@ struct TreeCompiler {
         int D = env[{u, w}].D;
         bond_node[{u, w}] = (int)C.nodes.size();
         C.nodes.push_back(make_desc({D, D}, bond_off));
+        C.nodes.back().reg_off = 0;
+        C.nodes.back().reg_len = 0;
       }
     // trajectory
     TreeDesc td{};
@@ -511,7 +531,14 @@ struct TreeCompiler {
     I.hist = hist(v, -1);
     I.sign = 1.0;
     I.flops = list_flops(li, C.nodes[I.node]);
+    set_regions(I, v, -1);
     C.prog.push_back(I);
+  }
+  void set_regions(Instr& I, int a, int b) {
+    I.rega_off = C.nodes[node0 + a].reg_off;
+    I.rega_len = C.nodes[node0 + a].reg_len;
+    I.regb_off = b >= 0 ? C.nodes[node0 + b].reg_off : 0;
+    I.regb_len = b >= 0 ? C.nodes[node0 + b].reg_len : 0;
   }
   void emit_qr(int v, int u) {
     Instr I{};
@@ -554,6 +581,7 @@ struct TreeCompiler {
     I.env_out = E.off;
     I.D = E.D;
     I.flops = list_flops(li, C.nodes[I.node]) + 8.0 * C.nodes[I.node].size * E.D * (1 + E.chans.size());
+    set_regions(I, u, -1);
     C.prog.push_back(I);
   }
   void emit_bond(int u, int w) {
@@ -597,6 +625,7 @@ struct TreeCompiler {
     I.hist = hist(u, w + 1000000);
     I.sign = -1.0;
     I.flops = list_flops(li, C.nodes[I.node]);
+    set_regions(I, u, w);
     if (!batched) I.team = TEAM_CLUSTER;
     C.prog.push_back(I);
   }

@@ -150,29 +150,49 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // All-reduce of nv (<= 8) per-thread values over the team.  Deterministic and
-// identical on every CTA.  Contains one team barrier.
+// identical on every CTA.  Contains one team barrier.  Cluster teams exchange the
+// per-CTA partials through distributed shared memory; the grid team through global memory.
 __device__ void team_allreduce(Team& tm, double* v, int nv) {
   __shared__ double s_w[NWARP * 8];
   __shared__ double s_out[8];
+  __shared__ double s_slot[2][8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = 0; i < nv; ++i) {
     double s = warp_sum(v[i]);
     if (lane == 0) s_w[warp * 8 + i] = s;
   }
   __syncthreads();
-  double* buf = tm.red + (long long)tm.parity * tm.red_stride;
-  if (threadIdx.x < nv) {
-    double s = 0;
-    for (int w = 0; w < NWARP; ++w) s += s_w[w * 8 + threadIdx.x];
-    buf[tm.rank * 8 + threadIdx.x] = s;
-  }
-  team_sync(tm);
-  if (warp == 0) {
-    for (int i = 0; i < nv; ++i) {
+  if (tm.kind == TEAM_CLUSTER) {
+    if (threadIdx.x < nv) {
       double s = 0;
-      for (int r = lane; r < tm.size; r += 32) s += buf[r * 8 + i];
-      s = warp_sum(s);
-      if (lane == 0) s_out[i] = s;
+      for (int w = 0; w < NWARP; ++w) s += s_w[w * 8 + threadIdx.x];
+      s_slot[tm.parity][threadIdx.x] = s;
+    }
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    if (warp == 0) {
+      for (int i = 0; i < nv; ++i) {
+        double s = 0;
+        if (lane < tm.size) s = *cl.map_shared_rank(&s_slot[tm.parity][i], lane);
+        s = warp_sum(s);
+        if (lane == 0) s_out[i] = s;
+      }
+    }
+  } else {
+    double* buf = tm.red + (long long)tm.parity * tm.red_stride;
+    if (threadIdx.x < nv) {
+      double s = 0;
+      for (int w = 0; w < NWARP; ++w) s += s_w[w * 8 + threadIdx.x];
+      buf[tm.rank * 8 + threadIdx.x] = s;
+    }
+    team_sync(tm);
+    if (warp == 0) {
+      for (int i = 0; i < nv; ++i) {
+        double s = 0;
+        for (int r = lane; r < tm.size; r += 32) s += buf[r * 8 + i];
+        s = warp_sum(s);
+        if (lane == 0) s_out[i] = s;
+      }
     }
   }
   __syncthreads();
@@ -235,84 +255,92 @@ __device__ __forceinline__ typename C2<T>::t mode_dot(const MT* row, int D, cons
   return a0;
 }
 
-// Operator matrices of one op, staged once in dynamic shared memory in the compute type.
-// slot[t][f] gives the shared offset of factor f of term t (-1: read from the pool).
-// Row-sparse constant operators are read from their tables in the pool (a few entries).
+// Staging of one op's operands in shared memory.  Every node's operators (the
+// environment blocks flowing into it and its constant operators) are contiguous in the
+// pool, so an op stages one or two regions with asynchronous 16-byte copies (cp.async),
+// plus its term list; a factor's shared-memory slot is its offset inside the staged
+// regions.  Matrices stay FP64 (double2) in shared memory and are converted on use.
 extern __shared__ __align__(16) unsigned char dyn_smem[];
-struct StageTable {
-  int slot[TTNS_MAX_TERMS][2];
-  int chan[16];
-  int end;        // first free element (compute type) after the staged matrices
+
+struct OpStage {
+  Term terms[TTNS_MAX_TERMS];
+  Factor chans[16];
+  long long a_off, b_off;  // pool offsets of the staged regions
+  int a_n, b_n;            // staged elements of each (a prefix when the region is larger)
+  int end;                 // first free double2 of the dynamic shared memory
 };
 
-template <typename T>
-__device__ void stage_matrices(const KernelParams& P, const NodeDesc& nd, const TermList& L, const Factor* chans,
-                               int nchan, StageTable& st) {
-  using V = typename C2<T>::t;
-  V* sm = reinterpret_cast<V*>(dyn_smem);
-  const long long cap = P.smem_bytes / (long long)sizeof(V);
+// one staging record per CTA, shared by every op (ops run one at a time)
+__shared__ OpStage s_os;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& L, const Factor* chans, int nchan,
+                         OpStage& os) {
+  double2* sm = reinterpret_cast<double2*>(dyn_smem);
+  const long long cap = P.smem_bytes / (long long)sizeof(double2) / 2;  // half for matrices, half for vectors
   __syncthreads();
   if (threadIdx.x == 0) {
-    long long off = 0;
-    for (int t = 0; t < L.count && t < TTNS_MAX_TERMS; ++t) {
-      const Term& T_ = P.terms[L.first + t];
-      for (int f = 0; f < 2; ++f) {
-        st.slot[t][f] = -1;
-        if (f < T_.nf && T_.f[f].nnz == 0) {
-          const long long need = (long long)nd.dims[T_.f[f].leg] * nd.dims[T_.f[f].leg];
-          if (off + need <= cap) { st.slot[t][f] = (int)off; off += need; }
-        }
-      }
-    }
-    for (int b = 0; b < 16; ++b) st.chan[b] = -1;
-    for (int b = 0; b < nchan && b < 16; ++b) {
-      if (chans[b].nnz != 0) continue;
-      const long long need = (long long)nd.dims[chans[b].leg] * nd.dims[chans[b].leg];
-      if (off + need <= cap) { st.chan[b] = (int)off; off += need; }
-    }
-    st.end = (int)((off + 1) & ~1LL);
+    const long long an = I.rega_len < cap ? I.rega_len : cap;
+    const long long rest = cap - an;
+    const long long bn = I.regb_len < rest ? I.regb_len : rest;
+    os.a_off = I.rega_off;
+    os.b_off = I.regb_off;
+    os.a_n = (int)an;
+    os.b_n = (int)bn;
+    os.end = (int)((an + bn + 1) & ~1LL);
   }
+  const int nt = L.count < TTNS_MAX_TERMS ? L.count : TTNS_MAX_TERMS;
+  for (int t = threadIdx.x; t < nt; t += NT) os.terms[t] = P.terms[L.first + t];
+  for (int b = threadIdx.x; b < nchan && b < 16; b += NT) os.chans[b] = chans[b];
   __syncthreads();
-  for (int t = 0; t < L.count && t < TTNS_MAX_TERMS; ++t) {
-    const Term& T_ = P.terms[L.first + t];
-    for (int f = 0; f < T_.nf; ++f) {
-      const int o = st.slot[t][f];
-      if (o < 0) continue;
-      const int n = nd.dims[T_.f[f].leg] * nd.dims[T_.f[f].leg];
-      const double2* src = P.pool + T_.f[f].mat;
-      for (int k = threadIdx.x; k < n; k += NT) sm[o + k] = cvt<T>(src[k]);
-    }
-  }
-  for (int b = 0; b < nchan && b < 16; ++b) {
-    const int o = st.chan[b];
-    if (o < 0) continue;
-    const int n = nd.dims[chans[b].leg] * nd.dims[chans[b].leg];
-    const double2* src = P.pool + chans[b].mat;
-    for (int k = threadIdx.x; k < n; k += NT) sm[o + k] = cvt<T>(src[k]);
-  }
+  for (int k = threadIdx.x; k < os.a_n; k += NT) cp_async16(sm + k, P.pool + os.a_off + k);
+  for (int k = threadIdx.x; k < os.b_n; k += NT) cp_async16(sm + os.a_n + k, P.pool + os.b_off + k);
+  cp_async_wait_all();
   __syncthreads();
+}
+
+__device__ __forceinline__ int fslot(const OpStage& os, const Factor& f, int D) {
+  const long long need = (long long)D * D;
+  long long e = f.mat - os.a_off;
+  if (e >= 0 && e + need <= os.a_n) return (int)e;
+  e = f.mat - os.b_off;
+  if (e >= 0 && e + need <= os.b_n) return os.a_n + (int)e;
+  return -1;
 }
 
 // Input vector staged in shared memory (compute type) after the matrices, when it fits.
 template <typename T>
-__device__ typename C2<T>::t* vec_smem(const KernelParams& P, const StageTable& st, long long N) {
+__device__ typename C2<T>::t* vec_smem(const KernelParams& P, const OpStage& os, long long N) {
   using V = typename C2<T>::t;
-  const long long cap = P.smem_bytes / (long long)sizeof(V);
-  if ((long long)st.end + N > cap) return nullptr;
-  return reinterpret_cast<V*>(dyn_smem) + st.end;
+  const long long avail = P.smem_bytes - (long long)os.end * (long long)sizeof(double2);
+  if (N * (long long)sizeof(V) > avail) return nullptr;
+  return reinterpret_cast<V*>(dyn_smem + (long long)os.end * sizeof(double2));
 }
 
 template <typename T>
 __device__ void stage_vector(typename C2<T>::t* dst, const double2* src, long long N) {
   __syncthreads();
-  for (long long k = threadIdx.x; k < N; k += NT) dst[k] = cvt<T>(src[k]);
+  long long k = threadIdx.x;
+  for (; k + 3 * NT < N; k += 4 * NT) {  // four independent loads in flight per thread
+    const double2 a = src[k], b = src[k + NT], c = src[k + 2 * NT], d = src[k + 3 * NT];
+    dst[k] = cvt<T>(a);
+    dst[k + NT] = cvt<T>(b);
+    dst[k + 2 * NT] = cvt<T>(c);
+    dst[k + 3 * NT] = cvt<T>(d);
+  }
+  for (; k < N; k += NT) dst[k] = cvt<T>(src[k]);
   __syncthreads();
 }
 
 // One factor applied at output idx: sum_k M[i][k] x[idx + (k - i) * stride] along the factor's leg.
 template <typename T, typename XT>
 __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, const NodeDesc& nd, const Factor& f,
-                                                        int slot, const XT* x, long long idx) {
+                                                        const OpStage& os, const XT* x, long long idx) {
   const LegPos lp = leg_pos(nd, f.leg, idx);
   const int D = nd.dims[f.leg];
   if (f.nnz > 0) {
@@ -327,8 +355,9 @@ __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, c
     }
     return acc;
   }
+  const int slot = fslot(os, f, D);
   if (slot >= 0) {
-    const typename C2<T>::t* sm = reinterpret_cast<const typename C2<T>::t*>(dyn_smem) + slot;
+    const double2* sm = reinterpret_cast<const double2*>(dyn_smem) + slot;
     return mode_dot<T>(sm + lp.i * D, D, x, lp.base, nd.strides[f.leg]);
   }
   return mode_dot<T>(P.pool + f.mat + (long long)lp.i * D, D, x, lp.base, nd.strides[f.leg]);
@@ -338,7 +367,7 @@ __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, c
 // factor applied at the shifted position.
 template <typename T, typename XT>
 __device__ __forceinline__ typename C2<T>::t direct_dot(const KernelParams& P, const NodeDesc& nd, const Term& T_,
-                                                        int dense_slot, const XT* x, long long idx) {
+                                                        const OpStage& os, const XT* x, long long idx) {
   using V = typename C2<T>::t;
   const Factor& sf = T_.f[T_.sparse_f];
   const Factor& df = T_.f[1 - T_.sparse_f];
@@ -352,7 +381,7 @@ __device__ __forceinline__ typename C2<T>::t direct_dot(const KernelParams& P, c
     const double2 v = vals[e];
     if (v.x == 0.0 && v.y == 0.0) continue;
     const long long idx2 = lp.base + (long long)((int)cols[e].x) * nd.strides[sf.leg];
-    const V d = factor_dot<T>(P, nd, df, dense_slot, x, idx2);
+    const V d = factor_dot<T>(P, nd, df, os, x, idx2);
     cmac<T>(acc, cvt<T>(v), d);
   }
   return acc;
@@ -361,15 +390,11 @@ __device__ __forceinline__ typename C2<T>::t direct_dot(const KernelParams& P, c
 // Stage 1: tmp[t] = first factor of two-stage term t applied to x (tmp in the compute type)
 template <typename T, typename XT>
 __device__ void apply_stage1(const KernelParams& P, Team& tm, const NodeDesc& nd, const XT* x, const TermList& L,
-                             typename C2<T>::t* tmp, long long tstride, const StageTable& st) {
+                             typename C2<T>::t* tmp, long long tstride, const OpStage& os) {
   const int t0 = L.count - L.n2;
-  const Term* terms = P.terms + L.first + t0;
   const long long N = nd.size;
   for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-    for (int t = 0; t < L.n2; ++t) {
-      const int tt = t0 + t;
-      tmp[t * tstride + idx] = factor_dot<T>(P, nd, terms[t].f[0], tt < TTNS_MAX_TERMS ? st.slot[tt][0] : -1, x, idx);
-    }
+    for (int t = 0; t < L.n2; ++t) tmp[t * tstride + idx] = factor_dot<T>(P, nd, os.terms[t0 + t].f[0], os, x, idx);
   }
 }
 
@@ -377,28 +402,24 @@ __device__ void apply_stage1(const KernelParams& P, Team& tm, const NodeDesc& nd
 template <typename T, typename XT>
 __device__ __forceinline__ typename C2<T>::t apply_stage2_at(const KernelParams& P, const NodeDesc& nd, const XT* x,
                                                             const TermList& L, const typename C2<T>::t* tmp,
-                                                            long long tstride, long long idx, const StageTable& st) {
+                                                            long long tstride, long long idx, const OpStage& os) {
   typename C2<T>::t acc;
   acc.x = 0;
   acc.y = 0;
-  const Term* terms = P.terms + L.first;
   const int n1 = L.count - L.n2 - L.nd;
   for (int t = 0; t < n1; ++t) {
-    const auto a = factor_dot<T>(P, nd, terms[t].f[0], t < TTNS_MAX_TERMS ? st.slot[t][0] : -1, x, idx);
+    const auto a = factor_dot<T>(P, nd, os.terms[t].f[0], os, x, idx);
     acc.x += a.x;
     acc.y += a.y;
   }
   for (int t = n1; t < n1 + L.nd; ++t) {
-    const int ds = t < TTNS_MAX_TERMS ? st.slot[t][1 - terms[t].sparse_f] : -1;
-    const auto a = direct_dot<T>(P, nd, terms[t], ds, x, idx);
+    const auto a = direct_dot<T>(P, nd, os.terms[t], os, x, idx);
     acc.x += a.x;
     acc.y += a.y;
   }
   const int t0 = L.count - L.n2;
   for (int t = 0; t < L.n2; ++t) {
-    const int tt = t0 + t;
-    const auto a = factor_dot<T>(P, nd, terms[tt].f[1], tt < TTNS_MAX_TERMS ? st.slot[tt][1] : -1, tmp + t * tstride,
-                                 idx);
+    const auto a = factor_dot<T>(P, nd, os.terms[t0 + t].f[1], os, tmp + t * tstride, idx);
     acc.x += a.x;
     acc.y += a.y;
   }
@@ -410,7 +431,7 @@ __device__ __forceinline__ typename C2<T>::t apply_stage2_at(const KernelParams&
 // b[1..m) with b[k] coupling k-1 and k), by a Chebyshev expansion on the Gershgorin
 // interval: exp(-i z X) = J_0(z) + 2 sum_n (-i)^n J_n(z) T_n(X), X = (T - c)/R, z = s R.
 // Runs on one warp (lane k holds component k, m <= 32); FP64 throughout.
-__device__ void texp_warp(const double* a, const double* b, int m, double s, double* ure, double* uim) {
+__device__ __noinline__ void texp_warp(const double* a, const double* b, int m, double s, double* ure, double* uim) {
   const int lane = threadIdx.x & 31;
   const bool on = lane < m;
   double ak = on ? a[lane] : 0.0;
@@ -517,6 +538,8 @@ struct KrylovShared {
   double uim[TTNS_KMAX];
   int flag;
 };
+__shared__ KrylovShared s_ks;
+
 
 struct PhaseClock {
   long long t;
@@ -533,9 +556,212 @@ struct PhaseClock {
   }
 };
 
+// Cluster-resident Krylov exponential for small nodes.  Each CTA of the cluster owns a
+// contiguous slice of every Krylov vector in its shared memory; the full input vector of
+// each application is all-gathered through distributed shared memory, every operator is
+// staged once, and the only global traffic is the node tensor in and out.  The arithmetic
+// is the same as op_expm's (same recurrence, same reductions, same convergence and
+// substep rules).
 template <typename T>
-__device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2* work, double tau) {
-  __shared__ KrylovShared ks;
+__device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, const Instr& I, double tau) {
+  using V = typename C2<T>::t;
+  KrylovShared& ks = s_ks;
+  OpStage& os = s_os;
+  PhaseClock pc;
+  pc.start(P.profile && tm.rank == 0 && threadIdx.x == 0);
+  const NodeDesc nd = P.nodes[I.node];
+  const TermList L = P.lists[I.terms];
+  const long long N = nd.size;
+  const int cs = tm.size;
+  const long long S = (N + cs - 1) / cs;           // slice length
+  const long long e0 = (long long)tm.rank * S;
+  const long long e1 = min(N, e0 + S);
+  const int mmax = min(P.mmax, (int)(N < (long long)TTNS_KMAX ? N : (long long)TTNS_KMAX));
+  // shared-memory layout after the matrices: [xs: N V][tmp: n2*N V][basis: (mmax+1)*S double2]
+  {
+    const long long mats = (long long)(I.rega_len + I.regb_len) * sizeof(double2);
+    long long off = (long long)(N + (long long)L.n2 * N) * sizeof(V);
+    off = (off + 15) & ~15LL;
+    const long long need = mats + 16 + off + (long long)(mmax + 1) * S * sizeof(double2);
+    if (need > P.smem_bytes) return false;  // same decision on every CTA (same sizes)
+  }
+  stage_op(P, I, L, nullptr, 0, os);
+  unsigned char* base = dyn_smem + ((long long)os.end * sizeof(double2));
+  V* xs = reinterpret_cast<V*>(base);
+  V* tmp = xs + N;
+  long long off = (long long)(N + (long long)L.n2 * N) * sizeof(V);
+  off = (off + 15) & ~15LL;
+  double2* basis = reinterpret_cast<double2*>(base + off);
+  cg::cluster_group cl = cg::this_cluster();
+  auto Ks = [&](int j) -> double2* { return basis + (long long)j * S; };
+  double2* x = P.pool + nd.off;
+  double s_rem = I.sign * tau / HBAR_EVFS;
+  int total_m = 0, m = 0;
+  for (long long e = e0 + threadIdx.x; e < e1; e += NT) Ks(0)[e - e0] = x[e];
+  __syncthreads();
+  pc.lap(P.ctl, 0);
+  for (int chunk = 0; chunk < 64; ++chunk) {
+    double v[1] = {0.0};
+    for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+      const double2 a = Ks(0)[e - e0];
+      v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
+    }
+    team_allreduce(tm, v, 1);
+    const double beta0 = sqrt(v[0]);
+    pc.lap(P.ctl, 6);
+    if (!(beta0 > 0.0)) {
+      if (!(beta0 == 0.0)) set_status(P.ctl, ST_NONFINITE, I.op, I.node);
+      break;
+    }
+    if (threadIdx.x == 0) {
+      ks.scale[0] = 1.0 / beta0;
+      ks.beta[0] = 0.0;
+    }
+    __syncthreads();
+    m = 0;
+    bool conv = false;
+    double bnext = 0.0, lead = 1.0;
+    int next_check = 1;
+    for (int j = 0; j < mmax; ++j) {
+      // all-gather K_j (complete on every CTA: written before the last cluster barrier)
+      {
+        long long e = threadIdx.x;
+        for (; e + 3 * NT < N; e += 4 * NT) {
+          double2 a[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const long long ee = e + q * NT;
+            const int r = (int)(ee / S);
+            a[q] = cl.map_shared_rank(Ks(j), r)[ee - (long long)r * S];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xs[e + q * NT] = cvt<T>(a[q]);
+        }
+        for (; e < N; e += NT) {
+          const int r = (int)(e / S);
+          xs[e] = cvt<T>(cl.map_shared_rank(Ks(j), r)[e - (long long)r * S]);
+        }
+      }
+      __syncthreads();
+      if (L.n2 > 0) {  // first factors of the two-stage terms, for the whole vector (redundant per CTA)
+        const int t0 = L.count - L.n2;
+        for (long long e = threadIdx.x; e < N; e += NT)
+          for (int t = 0; t < L.n2; ++t) tmp[t * N + e] = factor_dot<T>(P, nd, os.terms[t0 + t].f[0], os, xs, e);
+        __syncthreads();
+      }
+      pc.lap(P.ctl, 1);
+      const double sj = ks.scale[j], bj = ks.beta[j];
+      const double sjm = j > 0 ? ks.scale[j - 1] : 0.0;
+      double2* W = Ks(j + 1);
+      double part[1] = {0.0};
+      for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+        const auto a = apply_stage2_at<T>(P, nd, xs, L, tmp, N, e, os);
+        const double2 kj = Ks(j)[e - e0];
+        double wr = sj * (double)a.x, wi = sj * (double)a.y;
+        if (j > 0) {
+          const double2 km = Ks(j - 1)[e - e0];
+          wr = fma(-bj * sjm, km.x, wr);
+          wi = fma(-bj * sjm, km.y, wi);
+        }
+        W[e - e0] = make_double2(wr, wi);
+        part[0] = fma(kj.x, wr, fma(kj.y, wi, part[0]));
+      }
+      team_allreduce(tm, part, 1);
+      pc.lap(P.ctl, 2);
+      const double aj = part[0] * sj;
+      part[0] = 0.0;
+      for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+        const double2 kj = Ks(j)[e - e0];
+        double2 w = W[e - e0];
+        w.x = fma(-aj * sj, kj.x, w.x);
+        w.y = fma(-aj * sj, kj.y, w.y);
+        W[e - e0] = w;
+        part[0] = fma(w.x, w.x, fma(w.y, w.y, part[0]));
+      }
+      team_allreduce(tm, part, 1);
+      bnext = sqrt(part[0]);
+      pc.lap(P.ctl, 3);
+      if (threadIdx.x == 0) {
+        ks.alpha[j] = aj;
+        ks.beta[j + 1] = bnext;
+        ks.scale[j + 1] = bnext > 0.0 ? 1.0 / bnext : 0.0;
+      }
+      __syncthreads();
+      m = j + 1;
+      const double est = bnext * lead;
+      lead *= fabs(s_rem) * bnext / (double)m;
+      if ((est <= 1e3 * P.tol && m >= next_check) || m == mmax || !(bnext > 0.0)) {
+        next_check = m + 2;
+        if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s_rem, ks.ure, ks.uim);
+        __syncthreads();
+        const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);
+        const double err = bnext * um;
+        if (!(err == err)) {
+          set_status(P.ctl, ST_NONFINITE, I.op, I.node);
+          conv = true;
+        } else if (err <= P.tol || !(bnext > 0.0)) {
+          conv = true;
+        }
+        pc.lap(P.ctl, 4);
+        if (conv || m == mmax) break;
+      }
+    }
+    total_m += m;
+    double s_done = s_rem;
+    if (!conv && m < N) {
+      for (int k = 0; k < 30; ++k) {
+        s_done *= 0.5;
+        if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s_done, ks.ure, ks.uim);
+        __syncthreads();
+        const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);
+        __syncthreads();
+        if (bnext * um <= P.tol) break;
+      }
+      pc.lap(P.ctl, 4);
+    }
+    // y = beta0 sum_k u_k q_k into the own slice of K_0
+    double ny[1] = {0.0};
+    for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+      double yr = 0.0, yi = 0.0;
+      for (int k = 0; k < m; ++k) {
+        const double2 q = Ks(k)[e - e0];
+        const double sc = beta0 * ks.scale[k];
+        const double cr = ks.ure[k] * sc, ci = ks.uim[k] * sc;
+        yr = fma(cr, q.x, fma(-ci, q.y, yr));
+        yi = fma(cr, q.y, fma(ci, q.x, yi));
+      }
+      Ks(0)[e - e0] = make_double2(yr, yi);
+      ny[0] = fma(yr, yr, fma(yi, yi, ny[0]));
+    }
+    if (P.precision != 0) {
+      team_allreduce(tm, ny, 1);
+      const double ratio = ny[0] > 0.0 ? beta0 / sqrt(ny[0]) : 1.0;
+      if (fabs(ratio - 1.0) < 1e-3)
+        for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+          const double2 y = Ks(0)[e - e0];
+          Ks(0)[e - e0] = make_double2(y.x * ratio, y.y * ratio);
+        }
+    }
+    __syncthreads();
+    pc.lap(P.ctl, 5);
+    if (conv || m >= N || s_done == s_rem) break;
+    s_rem -= s_done;
+    if (chunk == 63 && tm.rank == 0 && threadIdx.x == 0) atomicAdd(&P.ctl->not_converged, 1ull);
+  }
+  for (long long e = e0 + threadIdx.x; e < e1; e += NT) x[e] = Ks(0)[e - e0];
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    P.mhist[I.hist] = m;
+    atomicAdd(&P.ctl->krylov_iters, (unsigned long long)total_m);
+    atomicAdd(&P.ctl->applies, (unsigned long long)total_m);
+    atomicAdd(&P.ctl->flops, I.flops * total_m);
+  }
+  team_sync(tm);
+  return true;
+}
+
+template <typename T>
+__device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2* work, double tau) {
+  KrylovShared& ks = s_ks;
   PhaseClock pc;
   pc.start(P.profile && tm.kind == TEAM_CLUSTER && tm.rank == 0 && threadIdx.x == 0);
   const NodeDesc nd = P.nodes[I.node];
@@ -547,9 +773,9 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
   auto* tmp = reinterpret_cast<typename C2<T>::t*>(work + (long long)P.mmax * kv);  // n_tmp temporaries
   auto Kp = [&](int j) -> double2* { return j == 0 ? x : Kb + (long long)(j - 1) * kv; };
   const int mmax = min(P.mmax, (int)(N < (long long)TTNS_KMAX ? N : (long long)TTNS_KMAX));
-  __shared__ StageTable st;
-  stage_matrices<T>(P, nd, L, nullptr, 0, st);
-  typename C2<T>::t* xs = vec_smem<T>(P, st, N);  // input vector in shared memory when it fits
+  OpStage& os = s_os;
+  stage_op(P, I, L, nullptr, 0, os);
+  typename C2<T>::t* xs = vec_smem<T>(P, os, N);  // input vector in shared memory when it fits
   pc.lap(P.ctl, 0);
   // exp(-i s H): s = time / hbar with the op's sign.  If the Krylov space of dimension
   // mmax does not reach the tolerance for the remaining time, the largest s / 2^k that
@@ -593,16 +819,16 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
       if (xs) stage_vector<T>(xs, Kj, N);
       if (L.n2 > 0) {
         if (xs)
-          apply_stage1<T>(P, tm, nd, xs, L, tmp, kv, st);
+          apply_stage1<T>(P, tm, nd, xs, L, tmp, kv, os);
         else
-          apply_stage1<T>(P, tm, nd, Kj, L, tmp, kv, st);
+          apply_stage1<T>(P, tm, nd, Kj, L, tmp, kv, os);
         team_sync(tm);
       }
       pc.lap(P.ctl, 1);
       double part[1] = {0.0};
       for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-        const auto a = xs ? apply_stage2_at<T>(P, nd, xs, L, tmp, kv, idx, st)
-                          : apply_stage2_at<T>(P, nd, Kj, L, tmp, kv, idx, st);
+        const auto a = xs ? apply_stage2_at<T>(P, nd, xs, L, tmp, kv, idx, os)
+                          : apply_stage2_at<T>(P, nd, Kj, L, tmp, kv, idx, os);
         const double2 kj = Kj[idx];
         double wr = sj * (double)a.x, wi = sj * (double)a.y;
         if (j > 0) {
@@ -668,6 +894,7 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
       pc.lap(P.ctl, 4);
     }
     // y = beta0 * sum_k u_k q_k written over x (each thread reads its own K_0 = x entries first)
+    double ny[1] = {0.0};
     for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
       double yr = 0.0, yi = 0.0;
       for (int k = 0; k < m; ++k) {
@@ -678,6 +905,19 @@ __device__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2
         yi = fma(cr, q.y, fma(ci, q.x, yi));
       }
       x[idx] = make_double2(yr, yi);
+      ny[0] = fma(yr, yr, fma(yi, yi, ny[0]));
+    }
+    if (P.precision != 0) {
+      // The exact exponential is unitary.  FP32-class contractions leave the Krylov basis
+      // orthonormal only to ~1e-7, so the combination's norm is restored to the input's.
+      team_allreduce(tm, ny, 1);
+      const double ratio = ny[0] > 0.0 ? beta0 / sqrt(ny[0]) : 1.0;
+      if (fabs(ratio - 1.0) < 1e-3) {
+        for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+          double2 y = x[idx];
+          x[idx] = make_double2(y.x * ratio, y.y * ratio);
+        }
+      }
     }
     team_sync(tm);
     pc.lap(P.ctl, 5);
@@ -705,6 +945,8 @@ struct QRShared {
   double2 coef[TTNS_MAX_D];
   double2 ph[TTNS_MAX_D];
 };
+__shared__ QRShared s_qs;
+
 
 __device__ __forceinline__ long long qr_addr(const NodeDesc& nd, int l, long long r, int c) {
   const long long st = nd.strides[l];
@@ -714,8 +956,8 @@ __device__ __forceinline__ long long qr_addr(const NodeDesc& nd, int l, long lon
 
 // Rows owned by a CTA of the team: r = rank*NT + t + k*nthr, t in [0, NT).
 // The helpers below walk them in a fixed order.
-__device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
-  __shared__ QRShared qs;
+__device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
+  QRShared& qs = s_qs;
   PhaseClock pc;
   pc.start(P.profile && tm.kind == TEAM_CLUSTER && tm.rank == 0 && threadIdx.x == 0);
   const NodeDesc nd = P.nodes[I.node];
@@ -950,7 +1192,7 @@ __device__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* 
 
 // ------------------------------------------------------------------ absorb
 // A_u <- R applied on leg I.leg (FP64), through a temporary
-__device__ void op_absorb(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
+__device__ __noinline__ void op_absorb(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
   const NodeDesc nd = P.nodes[I.node];
   const long long N = nd.size;
   double2* A = P.pool + nd.off;
@@ -970,7 +1212,7 @@ __device__ void op_absorb(const KernelParams& P, Team& tm, const Instr& I, doubl
 // env(u -> v): block 0 = Q^H (H-terms of u without v) Q, block 1+b = Q^H (channel factor b) Q,
 // contracted over every leg of Q except the leg toward v.
 template <typename T>
-__device__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
+__device__ __noinline__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
   const NodeDesc nd = P.nodes[I.node];
   const TermList L = P.lists[I.terms];
   const long long N = nd.size;
@@ -981,24 +1223,23 @@ __device__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2*
   const int l = I.leg;
   const int D = I.D;
   const int nb = 1 + I.nchan;
-  __shared__ StageTable st;
-  stage_matrices<T>(P, nd, L, P.chans + I.chan_first, I.nchan, st);
-  typename C2<T>::t* xs = vec_smem<T>(P, st, N);
+  OpStage& os = s_os;
+  stage_op(P, I, L, P.chans + I.chan_first, I.nchan, os);
+  typename C2<T>::t* xs = vec_smem<T>(P, os, N);
   if (xs) stage_vector<T>(xs, Q, N);
   if (L.n2 > 0) {
     if (xs)
-      apply_stage1<T>(P, tm, nd, xs, L, tmp, kv, st);
+      apply_stage1<T>(P, tm, nd, xs, L, tmp, kv, os);
     else
-      apply_stage1<T>(P, tm, nd, Q, L, tmp, kv, st);
+      apply_stage1<T>(P, tm, nd, Q, L, tmp, kv, os);
     team_sync(tm);
   }
   for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-    auto a = xs ? apply_stage2_at<T>(P, nd, xs, L, tmp, kv, idx, st) : apply_stage2_at<T>(P, nd, Q, L, tmp, kv, idx, st);
+    auto a = xs ? apply_stage2_at<T>(P, nd, xs, L, tmp, kv, idx, os) : apply_stage2_at<T>(P, nd, Q, L, tmp, kv, idx, os);
     Y[idx] = make_double2((double)a.x, (double)a.y);
     for (int b = 0; b < I.nchan; ++b) {
-      const Factor f = P.chans[I.chan_first + b];
-      auto c = xs ? factor_dot<T>(P, nd, f, b < 16 ? st.chan[b] : -1, xs, idx)
-                  : factor_dot<T>(P, nd, f, b < 16 ? st.chan[b] : -1, Q, idx);
+      const Factor& f = os.chans[b];
+      auto c = xs ? factor_dot<T>(P, nd, f, os, xs, idx) : factor_dot<T>(P, nd, f, os, Q, idx);
       Y[(long long)(1 + b) * kv + idx] = make_double2((double)c.x, (double)c.y);
     }
   }
@@ -1045,7 +1286,7 @@ __device__ void op_env(const KernelParams& P, Team& tm, const Instr& I, double2*
 }
 
 // ------------------------------------------------------------------ record rho_S
-__device__ void op_record(const KernelParams& P, Team& tm, const Instr& I, int* counter) {
+__device__ __noinline__ void op_record(const KernelParams& P, Team& tm, const Instr& I, int* counter) {
   const TreeDesc td = P.trees[I.tree];
   if (td.traj_off < 0) return;
   const NodeDesc nd = P.nodes[td.node0];
@@ -1101,7 +1342,8 @@ __device__ void exec_op(const KernelParams& P, Team& tm, const Instr& I, double2
   switch (I.op) {
     case OP_FWD:
     case OP_BOND:
-      op_expm<T>(P, tm, I, work, tau);
+      if (!(tm.kind == TEAM_CLUSTER && P.cluster_resident && op_expm_cluster<T>(P, tm, I, tau)))
+        op_expm<T>(P, tm, I, work, tau);
       break;
     case OP_QR:
       op_qr(P, tm, I, work);
@@ -1256,12 +1498,17 @@ __global__ void k_energy_partial(KernelParams P, int node, int terms, double* pa
   const double2* x = P.pool + nd.off;
   const long long N = nd.size;
   double e = 0, nn = 0;
-  __shared__ StageTable st;
-  if (threadIdx.x == 0)
-    for (int t = 0; t < TTNS_MAX_TERMS; ++t) st.slot[t][0] = st.slot[t][1] = -1;
+  OpStage& os = s_os;
+  const int nt = L.count < TTNS_MAX_TERMS ? L.count : TTNS_MAX_TERMS;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) os.terms[t] = P.terms[L.first + t];
+  if (threadIdx.x == 0) {
+    os.a_off = os.b_off = 0;
+    os.a_n = os.b_n = 0;
+    os.end = 0;
+  }
   __syncthreads();
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (long long)gridDim.x * blockDim.x) {
-    auto a = apply_stage2_at<double>(P, nd, x, L, P.work + (long long)P.mmax * P.kvec, P.kvec, idx, st);
+    auto a = apply_stage2_at<double>(P, nd, x, L, P.work + (long long)P.mmax * P.kvec, P.kvec, idx, os);
     double2 v = x[idx];
     e = fma(v.x, a.x, fma(v.y, a.y, e));
     nn = fma(v.x, v.x, fma(v.y, v.y, nn));

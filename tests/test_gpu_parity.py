@@ -122,7 +122,7 @@ def test_batched_trees_match_oracle(prec):
         bound = np.maximum(TOL[prec], 50 * env)
         assert np.all(err <= bound), f"{names[k]}: worst ratio {np.max(err / bound):.2f}"
         tr_norm = np.real(np.einsum("kii->k", tr))
-        assert np.abs(tr_norm - 1).max() < (1e-9 if prec == ttns.TTNS_FP64 else 1e-5)
+        assert np.abs(tr_norm - 1).max() < (1e-8 if prec == ttns.TTNS_FP64 else 1e-5)
     g.close()
 
 
