@@ -205,7 +205,7 @@ ttns_status ttns_selftest_wait_timeout(long long spin_limit, int* device_status)
  * locked memory pool or on threads that must not trigger an allocation).
  *   d_root   device pointer: rows x n_el complex (interleaved doubles), row-major,
  *            the electronic leg last (the root layout of ttns_get_node)
- *   rows     product of the root's bond dimensions, >= 1
+ *   rows     product of the root's bond dimensions, >= 1, with rows * n_el < 2^24
  *   n_el     1..16 electronic states
  *   d_rho    device pointer: n_el x n_el complex output, rho[s][s'] = sum_r A[r][s] conj(A[r][s'])
  *   cuda_stream  stream the two kernels are enqueued on (NULL = legacy default stream)

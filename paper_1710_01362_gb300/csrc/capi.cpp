@@ -180,6 +180,7 @@ static ttns_status check_tables(const Compiled& C, int mmax, long long kvec, lon
       sz *= nd.dims[k];
     }
     if (sz != nd.size || !in_pool(nd.off, nd.size) || nd.size > kvec) return fail(TTNS_E_INVALID, "table: node extent");
+    if (nd.size >= (1 << 24)) return fail(TTNS_E_INVALID, "table: a tensor has 2^24 or more elements");
   }
   auto check_factor = [&](const Factor& f, const NodeDesc& nd) {
     if (f.leg < 0 || f.leg >= nd.nl) return false;

@@ -36,6 +36,8 @@ struct NodeDesc {
   long long off;                 // offset of the tensor in the complex pool
   long long reg_off;             // operator region: the environment blocks flowing into this node
   int reg_len;                   // and its constant operators, contiguous (staged together)
+  float inv_dims[TTNS_MAX_LEGS];     // 1/dims and 1/strides for exact fast index division
+  float inv_strides[TTNS_MAX_LEGS];  // (indices stay below 2^24)
 };
 
 #define TTNS_SPARSE_MAX 4  // nonzeros per row of a constant operator stored in row-sparse form

@@ -393,6 +393,10 @@ struct TreeCompiler {
     d.off = off;
     d.reg_off = 0;
     d.reg_len = 0;
+    for (int k = 0; k < TTNS_MAX_LEGS; ++k) {
+      d.inv_dims[k] = k < d.nl ? 1.0f / (float)d.dims[k] : 0.0f;
+      d.inv_strides[k] = k < d.nl ? 1.0f / (float)d.strides[k] : 0.0f;
+    }
     return d;
   }
 

@@ -73,8 +73,8 @@ extern "C" ttns_status ttns_rho_from_root_noalloc(const double* d_root, long lon
                          "16 x 16 complex partial sums)");
     return TTNS_E_INVALID;
   }
-  if (rows < 1 || rows > INT_MAX / n_el) {
-    ttns::set_last_error("ttns_rho_from_root_noalloc: rows must be in 1..INT_MAX/n_el");
+  if (rows < 1 || rows * n_el >= (1LL << 24)) {
+    ttns::set_last_error("ttns_rho_from_root_noalloc: rows must be >= 1 with rows * n_el < 2^24");
     return TTNS_E_INVALID;
   }
   double* scratch = nullptr;
@@ -91,6 +91,10 @@ extern "C" ttns_status ttns_rho_from_root_noalloc(const double* d_root, long lon
   nd.strides[1] = 1;
   nd.size = (int)(rows * n_el);
   nd.off = 0;
+  nd.inv_dims[0] = 1.0f / (float)nd.dims[0];
+  nd.inv_dims[1] = 1.0f / (float)nd.dims[1];
+  nd.inv_strides[0] = 1.0f / (float)nd.strides[0];
+  nd.inv_strides[1] = 1.0f;
   long long nb = rows / 64;
   if (nb < 1) nb = 1;
   if (nb > TTNS_NOALLOC_MAX_BLOCKS) nb = TTNS_NOALLOC_MAX_BLOCKS;

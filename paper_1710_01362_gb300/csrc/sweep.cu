@@ -221,14 +221,28 @@ __device__ void team_finish_multi(Team& tm, int nval, double* out, double scale)
 
 // ------------------------------------------------------------------ sum-of-products apply
 // Position decomposition of flat index idx along leg l.
+// n / d for 0 <= n < 2^24 through a float reciprocal, corrected to the exact quotient
+// (the float estimate is within 2 of it); 64-bit integer division is emulated and slow.
+__device__ __forceinline__ int fdivu(int n, int d, float inv) {
+  int q = __float2int_rz((float)n * inv);
+  int r = n - q * d;
+  if (r < 0) { --q; r += d; }
+  if (r < 0) { --q; r += d; }
+  if (r >= d) { ++q; r -= d; }
+  if (r >= d) { ++q; }
+  return q;
+}
+
 struct LegPos {
   long long base;  // idx - i * stride
   int i;
 };
 __device__ __forceinline__ LegPos leg_pos(const NodeDesc& nd, int l, long long idx) {
-  int st = nd.strides[l];
-  int i = (int)((idx / st) % nd.dims[l]);
-  return LegPos{idx - (long long)i * st, i};
+  const int st = nd.strides[l], D = nd.dims[l];
+  const int n = (int)idx;
+  const int q = fdivu(n, st, nd.inv_strides[l]);
+  const int i = q - fdivu(q, D, nd.inv_dims[l]) * D;
+  return LegPos{(long long)(n - i * st), i};
 }
 
 // y_i = sum_k M[i][k] x[base + k*stride] with four independent accumulators.  M is a row
@@ -625,21 +639,22 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
     for (int j = 0; j < mmax; ++j) {
       // all-gather K_j (complete on every CTA: written before the last cluster barrier)
       {
-        long long e = threadIdx.x;
-        for (; e + 3 * NT < N; e += 4 * NT) {
+        const float invS = 1.0f / (float)S;
+        int e = threadIdx.x;
+        for (; e + 3 * NT < (int)N; e += 4 * NT) {
           double2 a[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            const long long ee = e + q * NT;
-            const int r = (int)(ee / S);
-            a[q] = cl.map_shared_rank(Ks(j), r)[ee - (long long)r * S];
+            const int ee = e + q * NT;
+            const int r = fdivu(ee, (int)S, invS);
+            a[q] = cl.map_shared_rank(Ks(j), r)[ee - r * (int)S];
           }
 #pragma unroll
           for (int q = 0; q < 4; ++q) xs[e + q * NT] = cvt<T>(a[q]);
         }
-        for (; e < N; e += NT) {
-          const int r = (int)(e / S);
-          xs[e] = cvt<T>(cl.map_shared_rank(Ks(j), r)[e - (long long)r * S]);
+        for (; e < (int)N; e += NT) {
+          const int r = fdivu(e, (int)S, invS);
+          xs[e] = cvt<T>(cl.map_shared_rank(Ks(j), r)[e - r * (int)S]);
         }
       }
       __syncthreads();
@@ -949,9 +964,10 @@ __shared__ QRShared s_qs;
 
 
 __device__ __forceinline__ long long qr_addr(const NodeDesc& nd, int l, long long r, int c) {
-  const long long st = nd.strides[l];
-  const long long p = r / st, q = r - p * st;
-  return p * nd.dims[l] * st + (long long)c * st + q;
+  const int st = nd.strides[l];
+  const int p = fdivu((int)r, st, nd.inv_strides[l]);
+  const int q = (int)r - p * st;
+  return (long long)(p * nd.dims[l] * st + c * st + q);
 }
 
 // Rows owned by a CTA of the team: r = rank*NT + t + k*nthr, t in [0, NT).
@@ -1265,7 +1281,7 @@ __device__ __noinline__ void op_env(const KernelParams& P, Team& tm, const Instr
       s.y = 0;
       const long long r1 = min(r_end, r0 + 64);
       for (long long r = r0; r < r1; ++r) {
-        const long long p = r / lst, q = r - p * lst;
+        const long long p = fdivu((int)r, (int)lst, nd.inv_strides[l]), q = r - p * lst;
         const long long base = p * D * lst + q;
         auto qa = ld<T>(Q + base + (long long)a * lst);
         auto y = ld<T>(Yb + base + (long long)a2 * lst);
@@ -1447,7 +1463,7 @@ __global__ void k_density_partial(const double2* pool, NodeDesc nd, int l, const
     const int b = o / D, b2 = o % D;
     double accr = 0, acci = 0;
     for (long long r = r_begin; r < r_end; ++r) {
-      const long long p = r / st, q = r - p * st;
+      const long long p = fdivu((int)r, (int)st, nd.inv_strides[l]), q = r - p * st;
       const long long base = p * D * st + q;
       const double2 y = A[base + (long long)b2 * st];
       double2 xa;
@@ -1456,7 +1472,8 @@ __global__ void k_density_partial(const double2* pool, NodeDesc nd, int l, const
       } else {
         // X[idx] = sum_a' rho_in[a'][a] A[a', ...] evaluated at idx = base + b*st (a = parent index)
         const long long idx = base + (long long)b * st;
-        const int a = (int)((idx / stp) % Dp);
+        const int qa = fdivu((int)idx, (int)stp, nd.inv_strides[0]);
+        const int a = qa - fdivu(qa, Dp, nd.inv_dims[0]) * Dp;
         const long long b0 = idx - (long long)a * stp;
         xa = make_double2(0, 0);
         for (int a2 = 0; a2 < Dp; ++a2) {
