@@ -73,6 +73,12 @@ typedef struct {
   long long spin_limit;  /* bound of every device-side wait, in SM clock cycles (0 -> 2e10);
                             a wait that runs out sets TTNS_E_TIMEOUT */
   int profile;           /* 1: accumulate per-op device time (see ttns_counters) */
+  int launch_flags;      /* bit 0: launch the persistent kernel as a plain cluster launch, without
+                            the cooperative attribute (for tools that do not keep the cluster shape
+                            of cooperative launches).  Co-residency of the grid then rests on the
+                            grid fitting an otherwise idle GPU; a grid barrier that cannot complete
+                            ends in TTNS_E_TIMEOUT.  A launch whose cluster shape or shared memory
+                            differs from the plan sets TTNS_E_CUDA before any work. */
 } ttns_options;
 
 /* One tree's Hamiltonian (Eq. 2) and truncation.

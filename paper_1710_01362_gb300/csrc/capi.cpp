@@ -13,7 +13,8 @@
 #include "model.h"
 
 namespace ttns {
-cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster, cudaStream_t stream);
+cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster, int cooperative,
+                         cudaStream_t stream);
 cudaError_t max_grid_for(int cluster, long long smem_bytes, int* grid);
 cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double* partials,
                            int nblocks, double* out, cudaStream_t st);
@@ -69,6 +70,14 @@ struct ttns_tree {
 static const char* kStatusNames[] = {"ok", "invalid", "oom", "cuda", "not converged", "timeout", "nonfinite", "io"};
 
 extern "C" const char* ttns_last_error(void) { return g_err.c_str(); }
+
+static std::string status_text(const Ctl& h) {
+  if (h.err_where == 300)
+    return std::string(kStatusNames[h.status]) + ": the persistent kernel ran with a cluster of " +
+           std::to_string(h.err_node) + " CTAs or less dynamic shared memory than planned";
+  return std::string(kStatusNames[h.status]) + " (op " + std::to_string(h.err_where) + ", node " +
+         std::to_string(h.err_node) + ")";
+}
 
 #define CUDA_TRY(x)                                                                          \
   do {                                                                                       \
@@ -264,6 +273,7 @@ static ttns_status plan_sizes(const Compiled& C, const ttns_options& o, Sizes* z
   per_cta = std::max<long long>(per_cta, 2LL * C.max_D * C.max_D);
   per_cta = std::max<long long>(per_cta, 2LL * (1 + z->maxchan) * C.max_D * C.max_D);
   per_cta = std::max<long long>(per_cta, 2LL * TTNS_MAX_D);
+  per_cta = std::max<long long>(per_cta, 2LL * (TTNS_KMAX + 1));  // reorthogonalisation dots
   z->per_cta = per_cta;
   return check_tables(C, z->mmax, z->kvec, per_cta, std::max(C.max_tmp, 1));
 }
@@ -280,6 +290,8 @@ static ttns_status device_init(ttns_tree* t) {
   if (t->cluster > 16) return fail(TTNS_E_INVALID, "cluster_ctas must be <= 16");
   int maxgrid = 0;
   const long long smem_bytes = 200 * 1024;
+  // the QR keeps three reduction buffers of 2 n^2 doubles (n <= TTNS_MAX_D) in it
+  static_assert(3LL * 2 * TTNS_MAX_D * TTNS_MAX_D * 8 <= 200 * 1024, "QR reduction buffers exceed the shared memory");
   CUDA_TRY(max_grid_for(t->cluster, smem_bytes, &maxgrid));
   if (maxgrid < t->cluster) return fail(TTNS_E_CUDA, "no co-resident cluster of the requested size");
   int grid = o.grid_ctas > 0 ? o.grid_ctas : maxgrid;
@@ -361,11 +373,12 @@ static ttns_status device_init(ttns_tree* t) {
   P.smem_bytes = smem_bytes;
   P.cluster_resident = 1;
   // initial environment pass
-  CUDA_TRY(launch_sweep(P, 0, t->grid, t->cluster, t->stream));
+  CUDA_TRY(launch_sweep(P, 0, t->grid, t->cluster, !(t->opt.launch_flags & 1), t->stream));
   CUDA_TRY(cudaStreamSynchronize(t->stream));
   Ctl h;
   CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-  if (h.status != 0) return fail((ttns_status)h.status, std::string("device status after the initial pass: ") + kStatusNames[h.status]);
+  if (h.status != 0)
+    return fail((ttns_status)h.status, std::string("device status after the initial pass: ") + status_text(h));
   return TTNS_OK;
 }
 
@@ -469,7 +482,7 @@ extern "C" ttns_status ttns_step(ttns_tree* t, double dt_fs, int n_steps) {
   if (n_steps == 0) return TTNS_OK;
   t->P.dt = dt_fs;
   t->P.n_steps = n_steps;
-  CUDA_TRY(launch_sweep(t->P, 1, t->grid, t->cluster, t->stream));
+  CUDA_TRY(launch_sweep(t->P, 1, t->grid, t->cluster, !(t->opt.launch_flags & 1), t->stream));
   t->t_fs += dt_fs * n_steps;
   return TTNS_OK;
 }
@@ -480,8 +493,7 @@ extern "C" ttns_status ttns_sync(ttns_tree* t) {
   Ctl h;
   CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
   if (h.status != 0)
-    return fail((ttns_status)h.status, std::string("device status: ") + kStatusNames[h.status] + " (op " +
-                                           std::to_string(h.err_where) + ", node " + std::to_string(h.err_node) + ")");
+    return fail((ttns_status)h.status, std::string("device status: ") + status_text(h));
   return TTNS_OK;
 }
 

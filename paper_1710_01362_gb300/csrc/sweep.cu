@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -32,6 +33,7 @@ namespace ttns {
 #define ST_TIMEOUT 5
 #define ST_NOT_CONVERGED 4
 #define ST_NONFINITE 6
+#define ST_LAUNCH 3       // the launch did not have the cluster shape / shared memory it was planned for
 
 __constant__ double c_inv[256];       // 1/n, c_inv[0] = 0
 __constant__ double c_invfact[128];   // 1/n!
@@ -293,9 +295,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+template <typename T>
 __device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& L, const Factor* chans, int nchan,
                          OpStage& os) {
-  double2* sm = reinterpret_cast<double2*>(dyn_smem);
   const long long cap = P.smem_bytes / (long long)sizeof(double2) / 2;  // half for matrices, half for vectors
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -312,9 +314,18 @@ __device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& 
   for (int t = threadIdx.x; t < nt; t += NT) os.terms[t] = P.terms[L.first + t];
   for (int b = threadIdx.x; b < nchan && b < 16; b += NT) os.chans[b] = chans[b];
   __syncthreads();
-  for (int k = threadIdx.x; k < os.a_n; k += NT) cp_async16(sm + k, P.pool + os.a_off + k);
-  for (int k = threadIdx.x; k < os.b_n; k += NT) cp_async16(sm + os.a_n + k, P.pool + os.b_off + k);
-  cp_async_wait_all();
+  if constexpr (std::is_same<T, double>::value) {
+    double2* sm = reinterpret_cast<double2*>(dyn_smem);
+    for (int k = threadIdx.x; k < os.a_n; k += NT) cp_async16(sm + k, P.pool + os.a_off + k);
+    for (int k = threadIdx.x; k < os.b_n; k += NT) cp_async16(sm + os.a_n + k, P.pool + os.b_off + k);
+    cp_async_wait_all();
+  } else {
+    // converted once here, so that the contractions read compute-type operands (a
+    // double -> float conversion per use would run on the FP64 pipe)
+    float2* sm = reinterpret_cast<float2*>(dyn_smem);
+    for (int k = threadIdx.x; k < os.a_n; k += NT) sm[k] = cvt<float>(__ldg(P.pool + os.a_off + k));
+    for (int k = threadIdx.x; k < os.b_n; k += NT) sm[os.a_n + k] = cvt<float>(__ldg(P.pool + os.b_off + k));
+  }
   __syncthreads();
 }
 
@@ -370,8 +381,8 @@ __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, c
     return acc;
   }
   const int slot = fslot(os, f, D);
-  if (slot >= 0) {
-    const double2* sm = reinterpret_cast<const double2*>(dyn_smem) + slot;
+  if (slot >= 0) {  // staged in the compute type
+    const typename C2<T>::t* sm = reinterpret_cast<const typename C2<T>::t*>(dyn_smem) + slot;
     return mode_dot<T>(sm + lp.i * D, D, x, lp.base, nd.strides[f.leg]);
   }
   return mode_dot<T>(P.pool + f.mat + (long long)lp.i * D, D, x, lp.base, nd.strides[f.leg]);
@@ -543,6 +554,45 @@ __device__ __noinline__ void texp_warp(const double* a, const double* b, int m, 
   if (on) { ure[lane] = rr; uim[lane] = ri; }
 }
 
+// Sum of nval doubles over the team, in a fixed order, identical on every CTA.  `mine`
+// holds this CTA's partials in shared memory and `out` receives the sums (shared memory).
+// Cluster teams read the other CTAs' partials through distributed shared memory: callers
+// alternate between two `mine` buffers, so that one cluster barrier per call suffices (a
+// buffer is rewritten only after the next call's barrier, which every reader has passed).
+// Grid teams go through the global partial buffers.
+__device__ void team_reduce_vec(Team& tm, const double* mine, double* out, int nval) {
+  __syncthreads();
+  if (tm.kind == TEAM_CLUSTER) {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    for (int k = threadIdx.x; k < nval; k += NT) {
+      double s = 0.0;
+      for (int r = 0; r < tm.size; ++r) s += *cl.map_shared_rank(mine + k, r);
+      out[k] = s;
+    }
+  } else {
+    double* buf = team_partials(tm);
+    for (int k = threadIdx.x; k < nval; k += NT) buf[(long long)tm.rank * nval + k] = mine[k];
+    team_sync(tm);
+    for (int k = threadIdx.x; k < nval; k += NT) {
+      double s = 0.0;
+      for (int r = 0; r < tm.size; ++r) s += buf[(long long)r * nval + k];
+      out[k] = s;
+    }
+    tm.parity ^= 1;
+  }
+  __syncthreads();
+}
+
+// Butterfly sum of NV values over a warp (every lane ends with a full sum; lane 0's is used).
+template <int NV>
+__device__ __forceinline__ void warp_sum_n(double* v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+}
+
 // ------------------------------------------------------------------ Lanczos exponential
 struct KrylovShared {
   double alpha[TTNS_KMAX + 1];
@@ -550,9 +600,115 @@ struct KrylovShared {
   double scale[TTNS_KMAX + 1];  // q_j = scale[j] * K_j
   double ure[TTNS_KMAX];
   double uim[TTNS_KMAX];
+  double rv[2][2 * (TTNS_KMAX + 1)];  // reorthogonalisation: per-CTA dot partials (alternating)
+  double rvo[2 * (TTNS_KMAX + 1)];    // and their team sums
   int flag;
 };
 __shared__ KrylovShared s_ks;
+
+// Full reorthogonalisation of the FP64 path (the oracle's Lanczos does the same): two
+// classical Gram-Schmidt passes of w = K_{j+1} against q_i = scale_i K_i, i = 0..j,
+//   w <- w - sum_i <q_i, w> q_i,  <q_i, w> = scale_i <K_i, w>.
+// The dots are team sums (fixed order); each pass costs one team reduction.  The
+// functions return this thread's share of |w|^2 after the second pass.
+//
+// Vectors in global memory, elements idx = gtid + k * nthr (op_expm):
+__device__ double reorth_strided(Team& tm, long long N, const double2* x, const double2* Kb, long long kv,
+                                 double2* W, int j, KrylovShared& ks) {
+  __shared__ double s_wp[NWARP][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto Kp = [&](int i) -> const double2* { return i == 0 ? x : Kb + (long long)(i - 1) * kv; };
+  double nrm = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    double* mine = ks.rv[pass];
+    for (int i0 = 0; i0 <= j; i0 += 8) {
+      const int ni = min(8, j + 1 - i0);
+      double acc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+      for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+        const double2 w = W[idx];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q < ni) {
+            const double2 k = Kp(i0 + q)[idx];
+            acc[2 * q] = fma(k.x, w.x, fma(k.y, w.y, acc[2 * q]));
+            acc[2 * q + 1] = fma(k.x, w.y, fma(-k.y, w.x, acc[2 * q + 1]));
+          }
+        }
+      }
+      warp_sum_n<16>(acc);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 16; ++q) s_wp[warp][q] = acc[q];
+      __syncthreads();
+      if (threadIdx.x < 2 * ni) {
+        double sum = 0.0;
+        for (int w = 0; w < NWARP; ++w) sum += s_wp[w][threadIdx.x];
+        mine[2 * i0 + threadIdx.x] = sum;
+      }
+      __syncthreads();
+    }
+    team_reduce_vec(tm, mine, ks.rvo, 2 * (j + 1));
+    nrm = 0.0;
+    for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
+      double2 w = W[idx];
+      for (int i = 0; i <= j; ++i) {
+        const double sc = ks.scale[i];
+        const double cr = sc * ks.rvo[2 * i], ci = sc * ks.rvo[2 * i + 1];  // <q_i, w>
+        const double2 k0 = Kp(i)[idx];
+        const double2 k = make_double2(sc * k0.x, sc * k0.y);             // q_i
+        w.x -= cr * k.x - ci * k.y;
+        w.y -= cr * k.y + ci * k.x;
+      }
+      W[idx] = w;
+      nrm = fma(w.x, w.x, fma(w.y, w.y, nrm));
+    }
+  }
+  return nrm;
+}
+
+// Slices in shared memory, elements [0, n_own) of every K_i slice (op_expm_cluster):
+__device__ double reorth_slices(Team& tm, const double2* basis, long long S, int n_own, int j, KrylovShared& ks) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double2* Kj1 = basis + (long long)(j + 1) * S;
+  double2* W = const_cast<double2*>(Kj1);
+  double nrm = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    double* mine = ks.rv[pass];
+    __syncthreads();  // w was written with the thread-strided mapping; the dots read it per lane
+    for (int i = warp; i <= j; i += NWARP) {  // warp per basis vector, lanes over the slice
+      const double2* Ki = basis + (long long)i * S;
+      double acc[2] = {0.0, 0.0};
+      for (int e = lane; e < n_own; e += 32) {
+        const double2 k = Ki[e], w = W[e];
+        acc[0] = fma(k.x, w.x, fma(k.y, w.y, acc[0]));
+        acc[1] = fma(k.x, w.y, fma(-k.y, w.x, acc[1]));
+      }
+      warp_sum_n<2>(acc);
+      if (lane == 0) {
+        mine[2 * i] = acc[0];
+        mine[2 * i + 1] = acc[1];
+      }
+    }
+    team_reduce_vec(tm, mine, ks.rvo, 2 * (j + 1));
+    nrm = 0.0;
+    for (int e = threadIdx.x; e < n_own; e += NT) {
+      double2 w = W[e];
+      for (int i = 0; i <= j; ++i) {
+        const double sc = ks.scale[i];
+        const double cr = sc * ks.rvo[2 * i], ci = sc * ks.rvo[2 * i + 1];  // <q_i, w>
+        const double2 k0 = basis[(long long)i * S + e];
+        const double2 k = make_double2(sc * k0.x, sc * k0.y);             // q_i
+        w.x -= cr * k.x - ci * k.y;
+        w.y -= cr * k.y + ci * k.x;
+      }
+      W[e] = w;
+      nrm = fma(w.x, w.x, fma(w.y, w.y, nrm));
+    }
+  }
+  return nrm;
+}
 
 
 struct PhaseClock {
@@ -596,16 +752,20 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
     const long long mats = (long long)(I.rega_len + I.regb_len) * sizeof(double2);
     long long off = (long long)(N + (long long)L.n2 * N) * sizeof(V);
     off = (off + 15) & ~15LL;
-    const long long need = mats + 16 + off + (long long)(mmax + 1) * S * sizeof(double2);
+    const long long need = mats + 16 + off + (long long)(mmax + 1) * S * sizeof(double2) + S * (long long)sizeof(V);
     if (need > P.smem_bytes) return false;  // same decision on every CTA (same sizes)
   }
-  stage_op(P, I, L, nullptr, 0, os);
+  stage_op<T>(P, I, L, nullptr, 0, os);
   unsigned char* base = dyn_smem + ((long long)os.end * sizeof(double2));
   V* xs = reinterpret_cast<V*>(base);
   V* tmp = xs + N;
   long long off = (long long)(N + (long long)L.n2 * N) * sizeof(V);
   off = (off + 15) & ~15LL;
   double2* basis = reinterpret_cast<double2*>(base + off);
+  // mixed precision: the own slice of the current Krylov vector in the compute type, which
+  // the other CTAs gather (converted once, by its owner)
+  constexpr bool kShadow = !std::is_same<T, double>::value;
+  V* kf = reinterpret_cast<V*>(basis + (long long)(mmax + 1) * S);
   cg::cluster_group cl = cg::this_cluster();
   auto Ks = [&](int j) -> double2* { return basis + (long long)j * S; };
   double2* x = P.pool + nd.off;
@@ -619,6 +779,7 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
     for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
       const double2 a = Ks(0)[e - e0];
       v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
+      if constexpr (kShadow) kf[e - e0] = cvt<T>(a);
     }
     team_allreduce(tm, v, 1);
     const double beta0 = sqrt(v[0]);
@@ -637,24 +798,26 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
     double bnext = 0.0, lead = 1.0;
     int next_check = 1;
     for (int j = 0; j < mmax; ++j) {
-      // all-gather K_j (complete on every CTA: written before the last cluster barrier)
+      // all-gather K_j (complete on every CTA: written before the last cluster barrier),
+      // from the compute-type slices in mixed precision
       {
+        V* src = kShadow ? kf : reinterpret_cast<V*>(Ks(j));
         const float invS = 1.0f / (float)S;
         int e = threadIdx.x;
         for (; e + 3 * NT < (int)N; e += 4 * NT) {
-          double2 a[4];
+          V a[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int ee = e + q * NT;
             const int r = fdivu(ee, (int)S, invS);
-            a[q] = cl.map_shared_rank(Ks(j), r)[ee - r * (int)S];
+            a[q] = cl.map_shared_rank(src, r)[ee - r * (int)S];
           }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) xs[e + q * NT] = cvt<T>(a[q]);
+          for (int q = 0; q < 4; ++q) xs[e + q * NT] = a[q];
         }
         for (; e < (int)N; e += NT) {
           const int r = fdivu(e, (int)S, invS);
-          xs[e] = cvt<T>(cl.map_shared_rank(Ks(j), r)[e - r * (int)S]);
+          xs[e] = cl.map_shared_rank(src, r)[e - r * (int)S];
         }
       }
       __syncthreads();
@@ -691,8 +854,10 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
         w.x = fma(-aj * sj, kj.x, w.x);
         w.y = fma(-aj * sj, kj.y, w.y);
         W[e - e0] = w;
+        if constexpr (kShadow) kf[e - e0] = cvt<T>(w);  // gathered after the next barrier
         part[0] = fma(w.x, w.x, fma(w.y, w.y, part[0]));
       }
+      if (P.precision == 0) part[0] = reorth_slices(tm, basis, S, (int)max(0LL, e1 - e0), j, ks);
       team_allreduce(tm, part, 1);
       bnext = sqrt(part[0]);
       pc.lap(P.ctl, 3);
@@ -789,8 +954,14 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
   auto Kp = [&](int j) -> double2* { return j == 0 ? x : Kb + (long long)(j - 1) * kv; };
   const int mmax = min(P.mmax, (int)(N < (long long)TTNS_KMAX ? N : (long long)TTNS_KMAX));
   OpStage& os = s_os;
-  stage_op(P, I, L, nullptr, 0, os);
-  typename C2<T>::t* xs = vec_smem<T>(P, os, N);  // input vector in shared memory when it fits
+  stage_op<T>(P, I, L, nullptr, 0, os);
+  using V = typename C2<T>::t;
+  V* xs = vec_smem<T>(P, os, N);  // input vector in shared memory when it fits
+  // otherwise, in mixed precision, a compute-type copy of the input vector in the workspace,
+  // written by the pass that produces the vector (FP64 Krylov basis, FP32 operand)
+  constexpr bool kShadow = !std::is_same<T, double>::value;
+  V* xf = reinterpret_cast<V*>(work + (long long)(P.mmax + P.n_tmp) * kv);
+  const bool shadow = kShadow && xs == nullptr;
   pc.lap(P.ctl, 0);
   // exp(-i s H): s = time / hbar with the op's sign.  If the Krylov space of dimension
   // mmax does not reach the tolerance for the remaining time, the largest s / 2^k that
@@ -804,6 +975,7 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
     for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
       const double2 a = x[idx];
       v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
+      if (shadow) xf[idx] = cvt<T>(a);
     }
     team_allreduce(tm, v, 1);
     const double beta0 = sqrt(v[0]);
@@ -832,18 +1004,16 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
       const double bj = ks.beta[j];
       const double sjm = j > 0 ? ks.scale[j - 1] : 0.0;
       if (xs) stage_vector<T>(xs, Kj, N);
+      // operand of this application: shared memory, the FP32 shadow, or K_j itself (FP64)
+      const V* xin = xs ? xs : (shadow ? xf : reinterpret_cast<const V*>(Kj));
       if (L.n2 > 0) {
-        if (xs)
-          apply_stage1<T>(P, tm, nd, xs, L, tmp, kv, os);
-        else
-          apply_stage1<T>(P, tm, nd, Kj, L, tmp, kv, os);
+        apply_stage1<T>(P, tm, nd, xin, L, tmp, kv, os);
         team_sync(tm);
       }
       pc.lap(P.ctl, 1);
       double part[1] = {0.0};
       for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-        const auto a = xs ? apply_stage2_at<T>(P, nd, xs, L, tmp, kv, idx, os)
-                          : apply_stage2_at<T>(P, nd, Kj, L, tmp, kv, idx, os);
+        const auto a = apply_stage2_at<T>(P, nd, xin, L, tmp, kv, idx, os);
         const double2 kj = Kj[idx];
         double wr = sj * (double)a.x, wi = sj * (double)a.y;
         if (j > 0) {
@@ -864,8 +1034,10 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
         w.x = fma(-aj * sj, kj.x, w.x);
         w.y = fma(-aj * sj, kj.y, w.y);
         W[idx] = w;
+        if (shadow) xf[idx] = cvt<T>(w);  // every read of the old shadow ended at the last barrier
         part[0] = fma(w.x, w.x, fma(w.y, w.y, part[0]));
       }
+      if (P.precision == 0) part[0] = reorth_strided(tm, N, x, Kb, kv, W, j, ks);
       team_allreduce(tm, part, 1);
       bnext = sqrt(part[0]);
       pc.lap(P.ctl, 3);
@@ -954,10 +1126,10 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
 // reflector and R_jj = 0; Q = H_0 ... H_{n-1} I[:, :n] through the compact WY form
 // Q = I - V T V^H; finally R_jj is made real and >= 0.  FP64.
 struct QRShared {
-  double tau[TTNS_MAX_D];
+  double tau[TTNS_MAX_D];    // H_j = I - tau_j v_j v_j^H with the unnormalised v_j of the column loop
+  double shat[TTNS_MAX_D];   // 1 / |v_j| = sqrt(tau_j / 2) (0 for an identity reflector)
   double2 vhead[TTNS_MAX_D];
   double2 rdiag[TTNS_MAX_D];
-  double2 coef[TTNS_MAX_D];
   double2 ph[TTNS_MAX_D];
 };
 __shared__ QRShared s_qs;
@@ -970,8 +1142,9 @@ __device__ __forceinline__ long long qr_addr(const NodeDesc& nd, int l, long lon
   return (long long)(p * nd.dims[l] * st + c * st + q);
 }
 
-// Rows owned by a CTA of the team: r = rank*NT + t + k*nthr, t in [0, NT).
-// The helpers below walk them in a fixed order.
+// Every CTA of the team owns a contiguous chunk of rows [rb, re); loops inside a CTA run
+// over (column, row) pairs so that small chunks (a few rows per CTA) still occupy the
+// threads.  The FP64 work is spread over all SMs of the team.
 __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
   QRShared& qs = s_qs;
   PhaseClock pc;
@@ -988,17 +1161,27 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   double2* G = P.cta_scratch + (long long)blockIdx.x * P.cta_scratch_stride;
   double2* Tm = G + TTNS_MAX_D * TTNS_MAX_D;
   double2* Z = Tm + TTNS_MAX_D * TTNS_MAX_D;
+  const long long chunk = (rows + tm.size - 1) / tm.size;
+  const long long rb = min(rows, (long long)tm.rank * chunk);
+  const long long re = min(rows, rb + chunk);
+  const int nr = (int)(re - rb);
+  const float inv_nr = nr > 0 ? 1.0f / (float)nr : 0.0f;
+  // reduction buffers in the dynamic shared memory (no operator is staged during a QR)
+  const int PB = 2 * n * n;
+  double* red[2] = {reinterpret_cast<double*>(dyn_smem), reinterpret_cast<double*>(dyn_smem) + PB};
+  double* redo = red[1] + PB;
+  int rp = 0;
   // copy and column-0 reduction: {fro^2, sigma_0^2, x0.re, x0.im}
   double v[4] = {0, 0, 0, 0};
-  for (long long r = tm.gtid(); r < rows; r += tm.nthr()) {
-    for (int c = 0; c < n; ++c) {
-      double2 a = A[qr_addr(nd, l, r, c)];
-      W[(long long)c * rows + r] = a;
-      v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
-      if (c == 0) {
-        v[1] = fma(a.x, a.x, fma(a.y, a.y, v[1]));
-        if (r == 0) { v[2] = a.x; v[3] = a.y; }
-      }
+  for (int idx = threadIdx.x; idx < n * nr; idx += NT) {
+    const int c = fdivu(idx, nr, inv_nr);
+    const long long r = rb + (idx - c * nr);
+    const double2 a = A[qr_addr(nd, l, r, c)];
+    W[(long long)c * rows + r] = a;
+    v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
+    if (c == 0) {
+      v[1] = fma(a.x, a.x, fma(a.y, a.y, v[1]));
+      if (r == 0) { v[2] = a.x; v[3] = a.y; }
     }
   }
   team_allreduce(tm, v, 4);
@@ -1006,8 +1189,6 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   const double thr = QR_NULL_REL * sqrt(v[0]);
   double sig2 = v[1];
   double2 x0 = make_double2(v[2], v[3]);
-  const long long r_cta0 = (long long)tm.rank * NT;
-  const long long r_step = (long long)tm.nthr();
   for (int j = 0; j < n; ++j) {
     const double sigma = sqrt(sig2);
     double tau = 0.0;
@@ -1023,59 +1204,62 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     }
     if (threadIdx.x == 0) {
       qs.tau[j] = tau;
+      qs.shat[j] = tau > 0.0 ? sqrt(0.5 * tau) : 0.0;
       qs.vhead[j] = vh;
       qs.rdiag[j] = alpha;
     }
     const int nk = n - j - 1;
+    const long long r0 = max(rb, (long long)j);  // own rows at or below the diagonal
+    const int nrr = (int)max(0LL, re - r0);
+    const double2* Vj = W + (long long)j * rows;
+    double nv[3] = {0, 0, 0};
     if (!null && nk > 0) {
-      // reduction B: c_k = tau sum_{r >= j} conj(v_r) W[k][r], k > j.  Warp w handles
-      // columns k = w, w + NWARP, ...; its lanes walk the CTA's rows.
-      double* part = team_partials(tm);
-      for (int k = warp; k < nk; k += NWARP) {
-        const double2* Wk = W + (long long)(j + 1 + k) * rows;
-        double ar = 0, ai = 0;
-        for (long long rb = r_cta0; rb < rows; rb += r_step) {
-          for (int t = lane; t < NT; t += 32) {
-            const long long r = rb + t;
-            if (r >= rows || r < j) continue;
-            const double2 vr = (r == j) ? vh : W[(long long)j * rows + r];
-            const double2 w = Wk[r];
-            ar = fma(vr.x, w.x, fma(vr.y, w.y, ar));
-            ai = fma(vr.x, w.y, fma(-vr.y, w.x, ai));
+      // c_k = tau sum_{r >= j} conj(v_r) W[k][r], k > j: warp w takes columns w, w + NWARP, ...
+      // (four at a time), its lanes the CTA's rows
+      double* mine = red[rp];
+      rp ^= 1;
+      for (int k0 = warp; k0 < nk; k0 += 4 * NWARP) {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (long long r = r0 + lane; r < re; r += 32) {
+          const double2 vr = (r == j) ? vh : Vj[r];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q * NWARP;
+            if (k < nk) {
+              const double2 w = W[(long long)(j + 1 + k) * rows + r];
+              acc[2 * q] = fma(vr.x, w.x, fma(vr.y, w.y, acc[2 * q]));
+              acc[2 * q + 1] = fma(vr.x, w.y, fma(-vr.y, w.x, acc[2 * q + 1]));
+            }
           }
         }
-        ar = warp_sum(ar);
-        ai = warp_sum(ai);
+        warp_sum_n<8>(acc);
         if (lane == 0) {
-          part[(long long)tm.rank * 2 * nk + 2 * k] = ar;
-          part[(long long)tm.rank * 2 * nk + 2 * k + 1] = ai;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int k = k0 + q * NWARP;
+            if (k < nk) {
+              mine[2 * k] = acc[2 * q];
+              mine[2 * k + 1] = acc[2 * q + 1];
+            }
+          }
         }
       }
-      __syncthreads();
-      team_sync(tm);
-      for (int k = threadIdx.x; k < 2 * nk; k += NT) {
-        double a = 0;
-        for (int r = 0; r < tm.size; ++r) a += part[(long long)r * 2 * nk + k];
-        if (k & 1) qs.coef[k >> 1].y = a * tau; else qs.coef[k >> 1].x = a * tau;
-      }
-      tm.parity ^= 1;
-      __syncthreads();
-      // update trailing columns and gather the next column's reduction
-      double nv[3] = {0, 0, 0};
-      for (long long r = tm.gtid(); r < rows; r += tm.nthr()) {
-        if (r < j) continue;
-        const double2 vr = (r == j) ? vh : W[(long long)j * rows + r];
-        for (int k = 0; k < nk; ++k) {
-          const double2 ck = qs.coef[k];
-          double2* wp = &W[(long long)(j + 1 + k) * rows + r];
-          double2 w = *wp;
-          w.x -= vr.x * ck.x - vr.y * ck.y;
-          w.y -= vr.x * ck.y + vr.y * ck.x;
-          *wp = w;
-          if (k == 0 && r >= j + 1) {
-            nv[0] = fma(w.x, w.x, fma(w.y, w.y, nv[0]));
-            if (r == j + 1) { nv[1] = w.x; nv[2] = w.y; }
-          }
+      team_reduce_vec(tm, mine, redo, 2 * nk);
+      // update the trailing columns on the own rows; gather the next column's reduction
+      const float inv_nrr = nrr > 0 ? 1.0f / (float)nrr : 0.0f;
+      for (int idx = threadIdx.x; idx < nk * nrr; idx += NT) {
+        const int k = fdivu(idx, nrr, inv_nrr);
+        const long long r = r0 + (idx - k * nrr);
+        const double2 vr = (r == j) ? vh : Vj[r];
+        const double2 ck = make_double2(tau * redo[2 * k], tau * redo[2 * k + 1]);
+        double2* wp = &W[(long long)(j + 1 + k) * rows + r];
+        double2 w = *wp;
+        w.x -= vr.x * ck.x - vr.y * ck.y;
+        w.y -= vr.x * ck.y + vr.y * ck.x;
+        *wp = w;
+        if (k == 0 && r >= j + 1) {
+          nv[0] = fma(w.x, w.x, fma(w.y, w.y, nv[0]));
+          if (r == j + 1) { nv[1] = w.x; nv[2] = w.y; }
         }
       }
       team_allreduce(tm, nv, 3);
@@ -1083,10 +1267,9 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
       x0 = make_double2(nv[1], nv[2]);
     } else if (nk > 0) {
       // no reflection: the next column's reduction on unchanged data
-      double nv[3] = {0, 0, 0};
-      for (long long r = tm.gtid(); r < rows; r += tm.nthr()) {
-        if (r < j + 1) continue;
-        const double2 w = W[(long long)(j + 1) * rows + r];
+      const double2* Wn = W + (long long)(j + 1) * rows;
+      for (long long r = max(rb, (long long)j + 1) + threadIdx.x; r < re; r += NT) {
+        const double2 w = Wn[r];
         nv[0] = fma(w.x, w.x, fma(w.y, w.y, nv[0]));
         if (r == j + 1) { nv[1] = w.x; nv[2] = w.y; }
       }
@@ -1097,49 +1280,60 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   }
   __syncthreads();
   pc.lap(P.ctl, 9);
-  // Gram of the Householder vectors: G[a][b] = v_a^H v_b over rows r >= max(a, b)
+  // Compact WY form Q = I - Vh T Vh^H, built from the unit-norm reflectors vh_j = v_j / |v_j|
+  // (tau = 2): a column just above the null threshold has |v_j| ~ 1e-8 |M| and tau_j ~ 1e16,
+  // and the unnormalised form would chain such factors through T and lose orthogonality.
+  // Gram of the unit reflectors: G[a][b] = vh_a^H vh_b over rows r >= max(a, b), a <= b;
+  // per pair a walk over the own rows with two accumulator sets
   {
-    double* part = team_partials(tm);
     const int n2 = n * n;
+    double* mine = red[rp];
+    rp ^= 1;
     for (int pidx = threadIdx.x; pidx < n2; pidx += NT) {
-      const int a = pidx / n, b = pidx % n;
-      double gr = 0, gi = 0;
+      const int a = pidx / n, b = pidx - (pidx / n) * n;
+      double g0r = 0, g0i = 0, g1r = 0, g1i = 0;
       if (a <= b && qs.tau[a] != 0.0 && qs.tau[b] != 0.0) {
-        for (long long rb = r_cta0; rb < rows; rb += r_step) {
-          const long long rend = min(rb + NT, rows);
-          for (long long r = max(rb, (long long)b); r < rend; ++r) {
-            const double2 va = (r == a) ? qs.vhead[a] : W[(long long)a * rows + r];
-            const double2 vb = (r == b) ? qs.vhead[b] : W[(long long)b * rows + r];
-            gr = fma(va.x, vb.x, fma(va.y, vb.y, gr));
-            gi = fma(va.x, vb.y, fma(-va.y, vb.x, gi));
-          }
+        const double2* Va = W + (long long)a * rows;
+        const double2* Vb = W + (long long)b * rows;
+        long long r = max(rb, (long long)b);
+        for (; r + 1 < re; r += 2) {
+          const double2 va0 = (r == a) ? qs.vhead[a] : Va[r];
+          const double2 vb0 = (r == b) ? qs.vhead[b] : Vb[r];
+          const double2 va1 = Va[r + 1];
+          const double2 vb1 = (r + 1 == b) ? qs.vhead[b] : Vb[r + 1];
+          g0r = fma(va0.x, vb0.x, fma(va0.y, vb0.y, g0r));
+          g0i = fma(va0.x, vb0.y, fma(-va0.y, vb0.x, g0i));
+          g1r = fma(va1.x, vb1.x, fma(va1.y, vb1.y, g1r));
+          g1i = fma(va1.x, vb1.y, fma(-va1.y, vb1.x, g1i));
+        }
+        if (r < re) {
+          const double2 va0 = (r == a) ? qs.vhead[a] : Va[r];
+          const double2 vb0 = (r == b) ? qs.vhead[b] : Vb[r];
+          g0r = fma(va0.x, vb0.x, fma(va0.y, vb0.y, g0r));
+          g0i = fma(va0.x, vb0.y, fma(-va0.y, vb0.x, g0i));
         }
       }
-      part[(long long)tm.rank * 2 * n2 + 2 * pidx] = gr;
-      part[(long long)tm.rank * 2 * n2 + 2 * pidx + 1] = gi;
+      mine[2 * pidx] = g0r + g1r;
+      mine[2 * pidx + 1] = g0i + g1i;
     }
-    __syncthreads();
-    team_sync(tm);
+    team_reduce_vec(tm, mine, redo, 2 * n2);
     for (int pidx = threadIdx.x; pidx < n2; pidx += NT) {
-      const int a = pidx / n, b = pidx % n;
+      const int a = pidx / n, b = pidx - (pidx / n) * n;
       if (a > b) continue;
-      double gr = 0, gi = 0;
-      for (int r = 0; r < tm.size; ++r) {
-        gr += part[(long long)r * 2 * n2 + 2 * pidx];
-        gi += part[(long long)r * 2 * n2 + 2 * pidx + 1];
-      }
+      const double sab = qs.shat[a] * qs.shat[b];
+      const double gr = sab * redo[2 * pidx], gi = sab * redo[2 * pidx + 1];
       G[a * TTNS_MAX_D + b] = make_double2(gr, gi);
       G[b * TTNS_MAX_D + a] = make_double2(gr, -gi);
     }
-    tm.parity ^= 1;
     __syncthreads();
   }
   pc.lap(P.ctl, 10);
-  // T (upper triangular): T[j][j] = tau_j, T[0:j, j] = -tau_j T[0:j, 0:j] G[0:j, j]
+  // T (upper triangular): T[j][j] = 2, T[0:j, j] = -2 T[0:j, 0:j] G[0:j, j] (rows and columns
+  // of identity reflectors stay zero)
   for (int idx = threadIdx.x; idx < n * n; idx += NT) Tm[idx / n * TTNS_MAX_D + idx % n] = make_double2(0, 0);
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    const double tj = qs.tau[j];
+    const double tj = qs.tau[j] != 0.0 ? 2.0 : 0.0;
     if (threadIdx.x < j && tj != 0.0) {
       const int i = threadIdx.x;
       double sr = 0, si = 0;
@@ -1154,18 +1348,21 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     if (threadIdx.x == 0) Tm[j * TTNS_MAX_D + j] = make_double2(tj, 0.0);
     __syncthreads();
   }
-  // Z = T V_top^H: Z[j][c] = sum_{j <= i <= c} T[j][i] conj(V[c][i])
+  // Z[j][c] = shat_j sum_{j <= i <= c} T[j][i] shat_i conj(V[c][i]), so that
+  // Q = I - V Z with the unnormalised V stored in the workspace
   for (int idx = threadIdx.x; idx < n * n; idx += NT) {
     const int j = idx / n, c = idx % n;
     double zr = 0, zi = 0;
     for (int i = j; i <= c; ++i) {
       if (qs.tau[i] == 0.0) continue;
       const double2 t = Tm[j * TTNS_MAX_D + i];
-      const double2 vci = (c == i) ? qs.vhead[i] : W[(long long)i * rows + c];
+      const double2 v = (c == i) ? qs.vhead[i] : W[(long long)i * rows + c];
+      const double si = qs.shat[i];
+      const double2 vci = make_double2(si * v.x, si * v.y);
       zr += t.x * vci.x + t.y * vci.y;
       zi += t.y * vci.x - t.x * vci.y;
     }
-    Z[j * TTNS_MAX_D + c] = make_double2(zr, zi);
+    Z[j * TTNS_MAX_D + c] = make_double2(qs.shat[j] * zr, qs.shat[j] * zi);
   }
   pc.lap(P.ctl, 11);
   // phases of the diagonal of R
@@ -1186,21 +1383,22 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
       Rout[idx] = make_double2(r.x * p.x + r.y * p.y, r.y * p.x - r.x * p.y);
     }
   }
-  // Q[r][c] = (delta_rc - sum_j V[r][j] Z[j][c]) * ph_c, written back into the tensor
-  for (long long r = tm.gtid(); r < rows; r += tm.nthr()) {
+  // Q[r][c] = (delta_rc - sum_j V[r][j] Z[j][c]) * ph_c over the own rows, one (c, r) pair
+  // per thread, written back into the tensor
+  for (int idx = threadIdx.x; idx < n * nr; idx += NT) {
+    const int c = fdivu(idx, nr, inv_nr);
+    const long long r = rb + (idx - c * nr);
     const int jmax = (int)(r < (long long)n - 1 ? r : (long long)n - 1);
-    for (int c = 0; c < n; ++c) {
-      double qre = (r == c) ? 1.0 : 0.0, qim = 0.0;
-      for (int j = 0; j <= jmax; ++j) {
-        if (qs.tau[j] == 0.0) continue;
-        const double2 vr = (r == j) ? qs.vhead[j] : W[(long long)j * rows + r];
-        const double2 z = Z[j * TTNS_MAX_D + c];
-        qre -= vr.x * z.x - vr.y * z.y;
-        qim -= vr.x * z.y + vr.y * z.x;
-      }
-      const double2 p = qs.ph[c];
-      A[qr_addr(nd, l, r, c)] = make_double2(qre * p.x - qim * p.y, qre * p.y + qim * p.x);
+    double qre = (r == c) ? 1.0 : 0.0, qim = 0.0;
+    for (int j = 0; j <= jmax; ++j) {
+      if (qs.tau[j] == 0.0) continue;
+      const double2 vr = (r == j) ? qs.vhead[j] : W[(long long)j * rows + r];
+      const double2 z = Z[j * TTNS_MAX_D + c];
+      qre -= vr.x * z.x - vr.y * z.y;
+      qim -= vr.x * z.y + vr.y * z.x;
     }
+    const double2 p = qs.ph[c];
+    A[qr_addr(nd, l, r, c)] = make_double2(qre * p.x - qim * p.y, qre * p.y + qim * p.x);
   }
   team_sync(tm);
   pc.lap(P.ctl, 12);
@@ -1233,31 +1431,37 @@ __device__ __noinline__ void op_env(const KernelParams& P, Team& tm, const Instr
   const TermList L = P.lists[I.terms];
   const long long N = nd.size;
   const long long kv = P.kvec;
+  using V = typename C2<T>::t;
   const double2* Q = P.pool + nd.off;
-  auto* tmp = reinterpret_cast<typename C2<T>::t*>(work + (long long)P.mmax * kv);
-  double2* Y = work;  // Y_0 .. Y_nchan at work + b*kv (fits: 1 + nchan <= mmax)
+  auto* tmp = reinterpret_cast<V*>(work + (long long)P.mmax * kv);
+  V* Y = reinterpret_cast<V*>(work);  // Y_0 .. Y_nchan at Y + b*kv, compute type (fits: 1 + nchan <= mmax)
   const int l = I.leg;
   const int D = I.D;
   const int nb = 1 + I.nchan;
   OpStage& os = s_os;
-  stage_op(P, I, L, P.chans + I.chan_first, I.nchan, os);
-  typename C2<T>::t* xs = vec_smem<T>(P, os, N);
-  if (xs) stage_vector<T>(xs, Q, N);
+  stage_op<T>(P, I, L, P.chans + I.chan_first, I.nchan, os);
+  V* xs = vec_smem<T>(P, os, N);
+  // the operand Q in the compute type: shared memory when it fits, else (mixed precision) a
+  // converted copy in the workspace, else (FP64) the tensor itself
+  const V* xq;
+  if (xs) {
+    stage_vector<T>(xs, Q, N);
+    xq = xs;
+  } else if constexpr (!std::is_same<T, double>::value) {
+    V* qf = reinterpret_cast<V*>(work + (long long)(P.mmax + P.n_tmp) * kv);
+    for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) qf[idx] = cvt<T>(Q[idx]);
+    team_sync(tm);
+    xq = qf;
+  } else {
+    xq = reinterpret_cast<const V*>(Q);
+  }
   if (L.n2 > 0) {
-    if (xs)
-      apply_stage1<T>(P, tm, nd, xs, L, tmp, kv, os);
-    else
-      apply_stage1<T>(P, tm, nd, Q, L, tmp, kv, os);
+    apply_stage1<T>(P, tm, nd, xq, L, tmp, kv, os);
     team_sync(tm);
   }
   for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-    auto a = xs ? apply_stage2_at<T>(P, nd, xs, L, tmp, kv, idx, os) : apply_stage2_at<T>(P, nd, Q, L, tmp, kv, idx, os);
-    Y[idx] = make_double2((double)a.x, (double)a.y);
-    for (int b = 0; b < I.nchan; ++b) {
-      const Factor& f = os.chans[b];
-      auto c = xs ? factor_dot<T>(P, nd, f, os, xs, idx) : factor_dot<T>(P, nd, f, os, Q, idx);
-      Y[(long long)(1 + b) * kv + idx] = make_double2((double)c.x, (double)c.y);
-    }
+    Y[idx] = apply_stage2_at<T>(P, nd, xq, L, tmp, kv, idx, os);
+    for (int b = 0; b < I.nchan; ++b) Y[(long long)(1 + b) * kv + idx] = factor_dot<T>(P, nd, os.chans[b], os, xq, idx);
   }
   team_sync(tm);
   // projection: out[b][a][a'] = sum_rows conj(Q[row, a]) Y_b[row, a']
@@ -1273,18 +1477,18 @@ __device__ __noinline__ void op_env(const KernelParams& P, Team& tm, const Instr
     const int b = o / (D * D);
     const int a = (o / D) % D;
     const int a2 = o % D;
-    const double2* Yb = Y + (long long)b * kv;
+    const V* Yb = Y + (long long)b * kv;
     double accr = 0, acci = 0;
     for (long long r0 = r_begin; r0 < r_end; r0 += 64) {
-      typename C2<T>::t s;
+      V s;
       s.x = 0;
       s.y = 0;
       const long long r1 = min(r_end, r0 + 64);
       for (long long r = r0; r < r1; ++r) {
         const long long p = fdivu((int)r, (int)lst, nd.inv_strides[l]), q = r - p * lst;
         const long long base = p * D * lst + q;
-        auto qa = ld<T>(Q + base + (long long)a * lst);
-        auto y = ld<T>(Yb + base + (long long)a2 * lst);
+        const V qa = xq[base + (long long)a * lst];
+        const V y = Yb[base + (long long)a2 * lst];
         s.x = fma(qa.x, y.x, fma(qa.y, y.y, s.x));
         s.y = fma(qa.x, y.y, fma(-qa.y, y.x, s.y));
       }
@@ -1436,7 +1640,28 @@ __device__ void run(const KernelParams& P, int phase) {
   if (prev == TEAM_CLUSTER) grid_sync(P.ctl, P.spin_limit);
 }
 
+__device__ __forceinline__ unsigned sreg_cluster_nctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned sreg_dynamic_smem_size() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
+
 __global__ void __launch_bounds__(NT, 1) k_sweep(KernelParams P, int phase) {
+  // Launch self-check before any barrier or distributed-shared-memory access: the
+  // interpreter addresses cluster peers by rank and stages operands up to smem_bytes, so a
+  // launch with another cluster shape or less dynamic shared memory returns an error
+  // status instead of running.  Every CTA takes the same decision.
+  const unsigned ncta = sreg_cluster_nctarank();
+  if (ncta != (unsigned)P.cluster_ctas || (long long)sreg_dynamic_smem_size() < P.smem_bytes ||
+      gridDim.x % (unsigned)P.cluster_ctas != 0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) set_status(P.ctl, ST_LAUNCH, 300, (int)ncta);
+    return;
+  }
   if (P.precision == 0)
     run<double>(P, phase);
   else
@@ -1590,7 +1815,8 @@ cudaError_t upload_constants() {
   return e;
 }
 
-cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster, cudaStream_t stream) {
+cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster, int cooperative,
+                         cudaStream_t stream) {
   cudaError_t e = upload_constants();
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_sweep, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -1610,7 +1836,7 @@ cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster
   at[1].id = cudaLaunchAttributeCooperative;
   at[1].val.cooperative = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 2;
+  cfg.numAttrs = cooperative ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, k_sweep, P, phase);
 }
 

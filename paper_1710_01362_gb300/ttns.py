@@ -41,7 +41,7 @@ class Options(C.Structure):
         ("cuda_stream", C.c_void_p), ("er_tree", C.c_int), ("D_er", C.c_int), ("init_state", C.c_int),
         ("psi_el", C.POINTER(C.c_double)), ("record", C.c_int), ("max_record", C.c_int),
         ("cluster_ctas", C.c_int), ("grid_ctas", C.c_int), ("grid_threshold", C.c_int),
-        ("spin_limit", C.c_longlong), ("profile", C.c_int),
+        ("spin_limit", C.c_longlong), ("profile", C.c_int), ("launch_flags", C.c_int),
     ]
 
 
@@ -189,7 +189,8 @@ def current_stream() -> Optional[int]:
 
 
 def _options(p0, precision, record=False, max_record=0, stream=None, cluster_ctas=0, grid_ctas=0,
-             krylov_tol=0.0, krylov_mmax=0, keep=None, grid_threshold=0, spin_limit=0, profile=0):
+             krylov_tol=0.0, krylov_mmax=0, keep=None, grid_threshold=0, spin_limit=0, profile=0,
+             launch_flags=0):
     psi = None
     if p0.psi_el is not None:
         arr = _cplx(p0.psi_el)
@@ -198,7 +199,7 @@ def _options(p0, precision, record=False, max_record=0, stream=None, cluster_cta
         psi = _dptr(arr)
     return Options(precision, krylov_tol, krylov_mmax, stream, int(p0.er_tree), int(p0.D_er),
                    int(p0.init_state), psi, int(record), int(max_record), cluster_ctas, grid_ctas,
-                   grid_threshold, spin_limit, profile)
+                   grid_threshold, spin_limit, profile, launch_flags)
 
 
 def plan(problems, precision: int = TTNS_MIXED, krylov_mmax: int = 0) -> dict:
@@ -224,7 +225,7 @@ class Tree:
     def __init__(self, problems, precision: int = TTNS_MIXED, record: bool = False, max_record: int = 0,
                  stream: Optional[int] = None, cluster_ctas: int = 0, grid_ctas: int = 0,
                  krylov_tol: float = 0.0, krylov_mmax: int = 0, grid_threshold: int = 0, spin_limit: int = 0,
-                 profile: bool = False):
+                 profile: bool = False, launch_flags: int = 0):
         single = not isinstance(problems, (list, tuple))
         probs = [problems] if single else list(problems)
         self.problems = probs
@@ -234,7 +235,7 @@ class Tree:
             stream = current_stream()
         self.opt = _options(probs[0], precision, record, max_record, stream, cluster_ctas, grid_ctas, krylov_tol,
                             krylov_mmax, keep=self._hold, grid_threshold=grid_threshold, spin_limit=spin_limit,
-                            profile=int(profile))
+                            profile=int(profile), launch_flags=int(launch_flags))
         h = C.c_void_p()
         arr = (ProblemC * len(probs))(*[k.c for k in self._keep])
         if len(probs) == 1:

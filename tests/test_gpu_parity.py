@@ -282,6 +282,19 @@ def test_repeated_runs_are_deterministic():
     assert np.array_equal(r[0], r[1])
 
 
+def test_plain_cluster_launch_equals_cooperative_launch():
+    # launch_flags bit 0 drops only the cooperative attribute: same grid, same clusters,
+    # same instruction stream, so the state is bitwise the same (grid team and cluster team)
+    p = W.sf_small(seed=7)
+    r = []
+    for flags in (0, 1):
+        g = ttns.Tree(p, precision=ttns.TTNS_MIXED, grid_threshold=64, launch_flags=flags)
+        g.step(p.dt, 4)
+        r.append(g.rho())
+        g.close()
+    assert np.array_equal(r[0], r[1])
+
+
 def test_bounded_wait_reports_timeout():
     # a grid barrier that one CTA never reaches (a flag nothing sets): the waiting CTA gives
     # up after the bound, the status word reads TTNS_E_TIMEOUT and the context stays usable
