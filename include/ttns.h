@@ -185,6 +185,9 @@ typedef struct {
   /* phases of the cluster-team QRs: 0 copy + norm, 1 column loop, 2 Gram of the
    * reflectors, 3 T and Z, 4 Q and R written back */
   double qr_phase_seconds[8];
+  /* the same two breakdowns for the grid-team (whole-GPU) operations */
+  double expm_phase_seconds_grid[8];
+  double qr_phase_seconds_grid[8];
 } ttns_counters;
 ttns_status ttns_get_counters(ttns_tree* tree, ttns_counters* out);
 

@@ -651,6 +651,8 @@ extern "C" ttns_status ttns_get_counters(ttns_tree* t, ttns_counters* out) {
     }
   for (int k = 0; k < 8; ++k) out->expm_phase_seconds[k] = h.phase_cycles[k] / hz;
   for (int k = 0; k < 8; ++k) out->qr_phase_seconds[k] = h.phase_cycles[8 + k] / hz;
+  for (int k = 0; k < 8; ++k) out->expm_phase_seconds_grid[k] = h.phase_cycles_grid[k] / hz;
+  for (int k = 0; k < 8; ++k) out->qr_phase_seconds_grid[k] = h.phase_cycles_grid[8 + k] / hz;
   return TTNS_OK;
 }
 

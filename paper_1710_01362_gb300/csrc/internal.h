@@ -118,6 +118,7 @@ struct Ctl {
   unsigned long long prof_cycles[8][2];  // per op code and team kind (rank-0 CTA clock cycles)
   unsigned long long prof_count[8][2];
   unsigned long long phase_cycles[16];   // phases of the Krylov exponential (0-7) and QR (8-15), cluster team
+  unsigned long long phase_cycles_grid[16];  // the same for grid-team ops
   unsigned progress;                     // bumped after every cluster-team instruction
   unsigned pad1;
 };

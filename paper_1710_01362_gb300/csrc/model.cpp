@@ -258,7 +258,8 @@ struct TreeCompiler {
     return off;
   }
   // constant operator: a dense matrix in the current region; when every row has few
-  // nonzeros, a row-sparse table is also built (placed after all regions, see finish_sparse)
+  // nonzeros, a row-sparse table is also built (placed at the end of the region, see
+  // finish_sparse)
   std::vector<std::pair<long long, std::vector<cplx>>> pending_sparse;
   long long push_operator(const std::vector<cplx>& m) {
     const long long off = push_matrix(m);
@@ -455,10 +456,10 @@ struct TreeCompiler {
         if (t.coups[k].va == v) opa_off[k] = push_operator(t.coups[k].opa);
         if (t.coups[k].vb == v) opb_off[k] = push_operator(t.coups[k].opb);
       }
+      finish_sparse();  // the node's row-sparse tables close its region (staged with it)
       C.nodes[node0 + v].reg_off = reg0;
       C.nodes[node0 + v].reg_len = (int)((long long)C.pool_init.size() - reg0);
     }
-    finish_sparse();
     bond_off = push_zeros((long long)TTNS_MAX_D * TTNS_MAX_D);
     // pseudo nodes for bond matrices
     for (int u = 0; u < n; ++u)

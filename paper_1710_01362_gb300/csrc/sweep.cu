@@ -151,56 +151,112 @@ __device__ __forceinline__ double warp_sum(double v) {
   return __shfl_sync(0xffffffffu, v, 0);
 }
 
-// All-reduce of nv (<= 8) per-thread values over the team.  Deterministic and
-// identical on every CTA.  Contains one team barrier.  Cluster teams exchange the
-// per-CTA partials through distributed shared memory; the grid team through global memory.
-__device__ void team_allreduce(Team& tm, double* v, int nv) {
-  __shared__ double s_w[NWARP * 8];
-  __shared__ double s_out[8];
-  __shared__ double s_slot[2][8];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i = 0; i < nv; ++i) {
-    double s = warp_sum(v[i]);
-    if (lane == 0) s_w[warp * 8 + i] = s;
-  }
-  __syncthreads();
-  if (tm.kind == TEAM_CLUSTER) {
-    if (threadIdx.x < nv) {
-      double s = 0;
-      for (int w = 0; w < NWARP; ++w) s += s_w[w * 8 + threadIdx.x];
-      s_slot[tm.parity][threadIdx.x] = s;
+template <int NV>
+__device__ __forceinline__ void warp_sum_n(double* v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+}
+
+// Sum of V values (a power of two <= 16) over a warp with V - 1 + 5 - log2(V) additions per
+// lane instead of 5 V: the first log2(V) butterfly levels exchange half of the remaining
+// values, the rest are plain.  Lane L returns the total of value warp_reduce_vid<V>(L); the
+// FP64 pipe, which also runs these additions, is the narrow one on this part.
+template <int V>
+__device__ __forceinline__ int warp_reduce_vid(int lane) {
+  int vid = 0;
+#pragma unroll
+  for (int n = V, off = 16; n > 1; n >>= 1, off >>= 1)
+    if (lane & off) vid += n / 2;
+  return vid;
+}
+template <int V>
+__device__ __forceinline__ double warp_reduce_t(double* v) {
+  const int lane = threadIdx.x & 31;
+  int off = 16;
+#pragma unroll
+  for (int n = V; n > 1; n >>= 1, off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const double send = hi ? v[i] : v[i + n / 2];
+      const double keep = hi ? v[i + n / 2] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
+  }
+  double t = v[0];
+#pragma unroll
+  for (; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+  return t;
+}
+
+// All-reduce of nv per-thread values over the team (up to four per barrier).  Deterministic
+// and identical on every CTA.  Inside a CTA the 256 values go through shared memory to warp
+// 0, which adds them in a fixed tree (7 additions per lane, then one transposing butterfly
+// for all values, instead of a butterfly per value on every warp: the additions run on the
+// narrow FP64 pipe).  Cluster teams push each CTA's totals into every peer's shared memory
+// before the cluster barrier, so that after it the sums come from local shared memory; the
+// grid team goes through global memory.
+static_assert(NT == 256, "team_allreduce assumes 256 threads per CTA");
+__device__ void team_allreduce4(Team& tm, double* v, int nv) {
+  __shared__ double s_all[4][NT];
+  __shared__ double s_out[4];
+  __shared__ double s_recv[2][16][4];  // [parity][source rank][value] (cluster teams, <= 16 CTAs)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s_all[i][threadIdx.x] = i < nv ? v[i] : 0.0;
+  __syncthreads();
+  double tot[4] = {0.0, 0.0, 0.0, 0.0};  // this CTA's totals (warp 0, every lane)
+  if (warp == 0) {
+    double t[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double* a = s_all[i];
+      t[i] = ((a[lane] + a[lane + 32]) + (a[lane + 64] + a[lane + 96])) +
+             ((a[lane + 128] + a[lane + 160]) + (a[lane + 192] + a[lane + 224]));
+    }
+    const double r = warp_reduce_t<4>(t);  // lanes 0, 8, 16, 24: values 0..3
+#pragma unroll
+    for (int i = 0; i < 4; ++i) tot[i] = __shfl_sync(0xffffffffu, r, 8 * i);
+  }
+  if (tm.kind == TEAM_CLUSTER) {
     cg::cluster_group cl = cg::this_cluster();
+    if (warp == 0 && lane < tm.size) {
+      double* dst = cl.map_shared_rank(&s_recv[tm.parity][tm.rank][0], lane);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dst[i] = tot[i];
+    }
     cl.sync();
     if (warp == 0) {
-      for (int i = 0; i < nv; ++i) {
-        double s = 0;
-        if (lane < tm.size) s = *cl.map_shared_rank(&s_slot[tm.parity][i], lane);
-        s = warp_sum(s);
-        if (lane == 0) s_out[i] = s;
-      }
+      double t[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[i] = lane < tm.size ? s_recv[tm.parity][lane][i] : 0.0;
+      const double r = warp_reduce_t<4>(t);
+      if ((lane & 7) == 0) s_out[lane >> 3] = r;
     }
   } else {
     double* buf = tm.red + (long long)tm.parity * tm.red_stride;
-    if (threadIdx.x < nv) {
-      double s = 0;
-      for (int w = 0; w < NWARP; ++w) s += s_w[w * 8 + threadIdx.x];
-      buf[tm.rank * 8 + threadIdx.x] = s;
-    }
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) buf[tm.rank * 4 + i] = tot[i];
     team_sync(tm);
     if (warp == 0) {
-      for (int i = 0; i < nv; ++i) {
-        double s = 0;
-        for (int r = lane; r < tm.size; r += 32) s += buf[r * 8 + i];
-        s = warp_sum(s);
-        if (lane == 0) s_out[i] = s;
-      }
+      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int r = lane; r < tm.size; r += 32)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) t[i] += buf[r * 4 + i];
+      const double r = warp_reduce_t<4>(t);
+      if ((lane & 7) == 0) s_out[lane >> 3] = r;
     }
   }
   __syncthreads();
   for (int i = 0; i < nv; ++i) v[i] = s_out[i];
-  __syncthreads();
   tm.parity ^= 1;
+}
+
+__device__ void team_allreduce(Team& tm, double* v, int nv) {
+  for (int i0 = 0; i0 < nv; i0 += 4) team_allreduce4(tm, v + i0, nv - i0 < 4 ? nv - i0 : 4);
 }
 
 // Multi-value all-reduce: every CTA has written nval partial doubles at
@@ -329,6 +385,15 @@ __device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& 
   __syncthreads();
 }
 
+// shared-memory position of n pool elements starting at pool offset off, or -1
+__device__ __forceinline__ int staged_at(const OpStage& os, long long off, long long n) {
+  long long e = off - os.a_off;
+  if (e >= 0 && e + n <= os.a_n) return (int)e;
+  e = off - os.b_off;
+  if (e >= 0 && e + n <= os.b_n) return os.a_n + (int)e;
+  return -1;
+}
+
 __device__ __forceinline__ int fslot(const OpStage& os, const Factor& f, int D) {
   const long long need = (long long)D * D;
   long long e = f.mat - os.a_off;
@@ -372,6 +437,17 @@ __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, c
     using V = typename C2<T>::t;
     V acc;
     acc.x = acc.y = (T)0;
+    const int sl = staged_at(os, f.sp, 2LL * D * f.nnz);
+    if (sl >= 0) {  // the table staged with the node's operators, in the compute type
+      const V* tab = reinterpret_cast<const V*>(dyn_smem) + sl;
+      const V* vals = tab + lp.i * f.nnz;
+      const V* cols = tab + D * f.nnz + lp.i * f.nnz;
+      for (int e = 0; e < f.nnz; ++e) {
+        const int k = (int)cols[e].x;
+        cmac<T>(acc, vals[e], cvt<T>(x[lp.base + (long long)k * nd.strides[f.leg]]));
+      }
+      return acc;
+    }
     const double2* vals = P.pool + f.sp + (long long)lp.i * f.nnz;
     const double2* cols = P.pool + f.sp + (long long)D * f.nnz + (long long)lp.i * f.nnz;
     for (int e = 0; e < f.nnz; ++e) {
@@ -398,10 +474,24 @@ __device__ __forceinline__ typename C2<T>::t direct_dot(const KernelParams& P, c
   const Factor& df = T_.f[1 - T_.sparse_f];
   const LegPos lp = leg_pos(nd, sf.leg, idx);
   const int Ds = nd.dims[sf.leg];
-  const double2* vals = P.pool + sf.sp + (long long)lp.i * sf.nnz;
-  const double2* cols = P.pool + sf.sp + (long long)Ds * sf.nnz + (long long)lp.i * sf.nnz;
   V acc;
   acc.x = acc.y = (T)0;
+  const int sl = staged_at(os, sf.sp, 2LL * Ds * sf.nnz);
+  if (sl >= 0) {  // staged table (compute type)
+    const V* tab = reinterpret_cast<const V*>(dyn_smem) + sl;
+    const V* vals = tab + lp.i * sf.nnz;
+    const V* cols = tab + Ds * sf.nnz + lp.i * sf.nnz;
+    for (int e = 0; e < sf.nnz; ++e) {
+      const V v = vals[e];
+      if (v.x == (T)0 && v.y == (T)0) continue;
+      const long long idx2 = lp.base + (long long)((int)cols[e].x) * nd.strides[sf.leg];
+      const V d = factor_dot<T>(P, nd, df, os, x, idx2);
+      cmac<T>(acc, v, d);
+    }
+    return acc;
+  }
+  const double2* vals = P.pool + sf.sp + (long long)lp.i * sf.nnz;
+  const double2* cols = P.pool + sf.sp + (long long)Ds * sf.nnz + (long long)lp.i * sf.nnz;
   for (int e = 0; e < sf.nnz; ++e) {
     const double2 v = vals[e];
     if (v.x == 0.0 && v.y == 0.0) continue;
@@ -585,14 +675,6 @@ __device__ void team_reduce_vec(Team& tm, const double* mine, double* out, int n
 }
 
 // Butterfly sum of NV values over a warp (every lane ends with a full sum; lane 0's is used).
-template <int NV>
-__device__ __forceinline__ void warp_sum_n(double* v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-}
-
 // ------------------------------------------------------------------ Lanczos exponential
 struct KrylovShared {
   double alpha[TTNS_KMAX + 1];
@@ -714,14 +796,16 @@ __device__ double reorth_slices(Team& tm, const double2* basis, long long S, int
 struct PhaseClock {
   long long t;
   bool on;
-  __device__ void start(bool enable) {
+  bool grid;  // phases of grid-team ops go to their own counters
+  __device__ void start(bool enable, bool grid_team = false) {
     on = enable;
+    grid = grid_team;
     t = clock64();
   }
   __device__ void lap(Ctl* ctl, int phase) {
     if (!on) return;
     const long long now = clock64();
-    atomicAdd(&ctl->phase_cycles[phase], (unsigned long long)(now - t));
+    atomicAdd(grid ? &ctl->phase_cycles_grid[phase] : &ctl->phase_cycles[phase], (unsigned long long)(now - t));
     t = now;
   }
 };
@@ -831,7 +915,10 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
       const double sj = ks.scale[j], bj = ks.beta[j];
       const double sjm = j > 0 ? ks.scale[j - 1] : 0.0;
       double2* W = Ks(j + 1);
-      double part[1] = {0.0};
+      // part[0] = Re <K_j, w>; in mixed precision also part[1] = |w|^2, so that one team
+      // reduction gives both alpha_j and beta_{j+1}
+      const bool mixed = P.precision != 0;
+      double part[3] = {0.0, 0.0, 0.0};
       for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
         const auto a = apply_stage2_at<T>(P, nd, xs, L, tmp, N, e, os);
         const double2 kj = Ks(j)[e - e0];
@@ -843,11 +930,21 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
         }
         W[e - e0] = make_double2(wr, wi);
         part[0] = fma(kj.x, wr, fma(kj.y, wi, part[0]));
+        if (mixed) {
+          part[1] = fma(wr, wr, fma(wi, wi, part[1]));
+          part[2] = fma(kj.x, kj.x, fma(kj.y, kj.y, part[2]));
+        }
       }
-      team_allreduce(tm, part, 1);
+      team_allreduce(tm, part, mixed ? 3 : 1);
       pc.lap(P.ctl, 2);
       const double aj = part[0] * sj;
-      part[0] = 0.0;
+      // |w - alpha_j q_j|^2 = |w|^2 - 2 alpha_j^2 + alpha_j^2 |q_j|^2 with |q_j|^2 from the same
+      // reduction (the error of an assumed |q_j| = 1 would grow by alpha^2 / beta^2 per step);
+      // used unless it cancels (the same decision on every CTA)
+      const double nq = sj * sj * part[2];
+      const double b2 = part[1] - aj * aj * (2.0 - nq);
+      const bool fused = mixed && b2 > 1e-4 * part[1];
+      double nrm[1] = {0.0};
       for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
         const double2 kj = Ks(j)[e - e0];
         double2 w = W[e - e0];
@@ -855,11 +952,16 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
         w.y = fma(-aj * sj, kj.y, w.y);
         W[e - e0] = w;
         if constexpr (kShadow) kf[e - e0] = cvt<T>(w);  // gathered after the next barrier
-        part[0] = fma(w.x, w.x, fma(w.y, w.y, part[0]));
+        nrm[0] = fma(w.x, w.x, fma(w.y, w.y, nrm[0]));
       }
-      if (P.precision == 0) part[0] = reorth_slices(tm, basis, S, (int)max(0LL, e1 - e0), j, ks);
-      team_allreduce(tm, part, 1);
-      bnext = sqrt(part[0]);
+      if (P.precision == 0) nrm[0] = reorth_slices(tm, basis, S, (int)max(0LL, e1 - e0), j, ks);
+      if (fused) {
+        bnext = sqrt(b2);
+        cl.sync();  // the slices of K_{j+1} are complete before any CTA gathers them
+      } else {
+        team_allreduce(tm, nrm, 1);
+        bnext = sqrt(nrm[0]);
+      }
       pc.lap(P.ctl, 3);
       if (threadIdx.x == 0) {
         ks.alpha[j] = aj;
@@ -943,7 +1045,7 @@ template <typename T>
 __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2* work, double tau) {
   KrylovShared& ks = s_ks;
   PhaseClock pc;
-  pc.start(P.profile && tm.kind == TEAM_CLUSTER && tm.rank == 0 && threadIdx.x == 0);
+  pc.start(P.profile && tm.rank == 0 && threadIdx.x == 0, tm.kind == TEAM_GRID);
   const NodeDesc nd = P.nodes[I.node];
   const TermList L = P.lists[I.terms];
   const long long N = nd.size;
@@ -1011,7 +1113,10 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
         team_sync(tm);
       }
       pc.lap(P.ctl, 1);
-      double part[1] = {0.0};
+      // part[0] = Re <K_j, w>; in mixed precision also part[1] = |w|^2 (one reduction for
+      // alpha_j and beta_{j+1}, as in the cluster-resident form)
+      const bool mixed = P.precision != 0;
+      double part[3] = {0.0, 0.0, 0.0};
       for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
         const auto a = apply_stage2_at<T>(P, nd, xin, L, tmp, kv, idx, os);
         const double2 kj = Kj[idx];
@@ -1023,11 +1128,21 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
         }
         W[idx] = make_double2(wr, wi);
         part[0] = fma(kj.x, wr, fma(kj.y, wi, part[0]));  // Re(conj(K_j) w)
+        if (mixed) {
+          part[1] = fma(wr, wr, fma(wi, wi, part[1]));
+          part[2] = fma(kj.x, kj.x, fma(kj.y, kj.y, part[2]));
+        }
       }
-      team_allreduce(tm, part, 1);
+      team_allreduce(tm, part, mixed ? 3 : 1);
       pc.lap(P.ctl, 2);
       const double aj = part[0] * sj;
-      part[0] = 0.0;
+      // |w - alpha_j q_j|^2 = |w|^2 - 2 alpha_j^2 + alpha_j^2 |q_j|^2 with |q_j|^2 from the same
+      // reduction (the error of an assumed |q_j| = 1 would grow by alpha^2 / beta^2 per step);
+      // used unless it cancels (the same decision on every CTA)
+      const double nq = sj * sj * part[2];
+      const double b2 = part[1] - aj * aj * (2.0 - nq);
+      const bool fused = mixed && b2 > 1e-4 * part[1];
+      double nrm[1] = {0.0};
       for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
         const double2 kj = Kj[idx];
         double2 w = W[idx];
@@ -1035,11 +1150,16 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
         w.y = fma(-aj * sj, kj.y, w.y);
         W[idx] = w;
         if (shadow) xf[idx] = cvt<T>(w);  // every read of the old shadow ended at the last barrier
-        part[0] = fma(w.x, w.x, fma(w.y, w.y, part[0]));
+        nrm[0] = fma(w.x, w.x, fma(w.y, w.y, nrm[0]));
       }
-      if (P.precision == 0) part[0] = reorth_strided(tm, N, x, Kb, kv, W, j, ks);
-      team_allreduce(tm, part, 1);
-      bnext = sqrt(part[0]);
+      if (P.precision == 0) nrm[0] = reorth_strided(tm, N, x, Kb, kv, W, j, ks);
+      if (fused) {
+        bnext = sqrt(b2);
+        team_sync(tm);  // K_{j+1} and its shadow are complete before the next application
+      } else {
+        team_allreduce(tm, nrm, 1);
+        bnext = sqrt(nrm[0]);
+      }
       pc.lap(P.ctl, 3);
       if (threadIdx.x == 0) {
         ks.alpha[j] = aj;
@@ -1128,6 +1248,7 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
 struct QRShared {
   double tau[TTNS_MAX_D];    // H_j = I - tau_j v_j v_j^H with the unnormalised v_j of the column loop
   double shat[TTNS_MAX_D];   // 1 / |v_j| = sqrt(tau_j / 2) (0 for an identity reflector)
+  double2 coef[TTNS_MAX_D];  // tau_j v_j^H W[k] of the trailing columns
   double2 vhead[TTNS_MAX_D];
   double2 rdiag[TTNS_MAX_D];
   double2 ph[TTNS_MAX_D];
@@ -1148,7 +1269,7 @@ __device__ __forceinline__ long long qr_addr(const NodeDesc& nd, int l, long lon
 __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr& I, double2* work) {
   QRShared& qs = s_qs;
   PhaseClock pc;
-  pc.start(P.profile && tm.kind == TEAM_CLUSTER && tm.rank == 0 && threadIdx.x == 0);
+  pc.start(P.profile && tm.rank == 0 && threadIdx.x == 0, tm.kind == TEAM_GRID);
   const NodeDesc nd = P.nodes[I.node];
   const int l = I.leg;
   const int n = nd.dims[l];
@@ -1167,29 +1288,86 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   const int nr = (int)(re - rb);
   const float inv_nr = nr > 0 ? 1.0f / (float)nr : 0.0f;
   // reduction buffers in the dynamic shared memory (no operator is staged during a QR)
-  const int PB = 2 * n * n;
+  const int PB = max(2 * n * n, 4 * n + 4);
   double* red[2] = {reinterpret_cast<double*>(dyn_smem), reinterpret_cast<double*>(dyn_smem) + PB};
   double* redo = red[1] + PB;
   int rp = 0;
-  // copy and column-0 reduction: {fro^2, sigma_0^2, x0.re, x0.im}
-  double v[4] = {0, 0, 0, 0};
+  // the CTA's own rows of the workspace matrix stay in shared memory during the QR when
+  // they fit (column-major, `chunk` rows per column); rows < n, which other CTAs read for T,
+  // Z and R, are also written to the global workspace after the column loop
+  const long long ws_off = (3LL * PB * (long long)sizeof(double) + 15) & ~15LL;
+  const bool in_smem = ws_off + (long long)n * chunk * (long long)sizeof(double2) <= P.smem_bytes;
+  double2* const Wl = in_smem ? reinterpret_cast<double2*>(dyn_smem + ws_off) : W;
+  const long long ldw = in_smem ? chunk : rows;
+  const long long roff = in_smem ? rb : 0;
+  auto WA = [&](int c, long long r) -> double2& { return Wl[(long long)c * ldw + (r - roff)]; };
+  // copy into the column-major workspace; the Frobenius norm sets the null threshold
+  double fro = 0.0;
   for (int idx = threadIdx.x; idx < n * nr; idx += NT) {
     const int c = fdivu(idx, nr, inv_nr);
     const long long r = rb + (idx - c * nr);
     const double2 a = A[qr_addr(nd, l, r, c)];
-    W[(long long)c * rows + r] = a;
-    v[0] = fma(a.x, a.x, fma(a.y, a.y, v[0]));
-    if (c == 0) {
-      v[1] = fma(a.x, a.x, fma(a.y, a.y, v[1]));
-      if (r == 0) { v[2] = a.x; v[3] = a.y; }
-    }
+    WA(c, r) = a;
+    fro = fma(a.x, a.x, fma(a.y, a.y, fro));
   }
-  team_allreduce(tm, v, 4);
+  __syncthreads();  // copied with the pair mapping, read below per lane
+  // One team reduction per column.  Before reflecting column j every CTA needs, over its
+  // rows r > j and for the columns c = j .. n-1,
+  //   d_c = sum_r conj(W[j][r]) W[c][r]   and   h_c = W[c][j]  (row j: its owner only),
+  // in slots [4 (c - j) .. 4 (c - j) + 4).  Then sigma_j^2 = |h_j|^2 + d_j, x0 = h_j, and
+  // c_k = tau (d_k + conj(vh) h_k) is v^H W[k] with the head of v replaced by vh.
+  auto prepare = [&](int jj, double* mine) {
+    const int nc = n - jj;
+    const long long r1 = max(rb, (long long)jj + 1);
+    for (int c0 = 0; c0 < nc; c0 += 4 * NWARP) {
+      double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (long long r = r1 + lane; r < re; r += 32) {
+        const double2 vr = WA(jj, r);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = c0 + warp + q * NWARP;
+          if (c < nc) {
+            const double2 w = WA(jj + c, r);
+            acc[2 * q] = fma(vr.x, w.x, fma(vr.y, w.y, acc[2 * q]));
+            acc[2 * q + 1] = fma(vr.x, w.y, fma(-vr.y, w.x, acc[2 * q + 1]));
+          }
+        }
+      }
+      const double t = warp_reduce_t<8>(acc);
+      if ((lane & 3) == 0) {
+        const int vid = warp_reduce_vid<8>(lane);
+        const int c = c0 + warp + (vid >> 1) * NWARP;
+        if (c < nc) mine[4 * c + (vid & 1)] = t;
+      }
+    }
+    const bool own_row = rb <= jj && jj < re;
+    for (int c = threadIdx.x; c < nc; c += NT) {
+      const double2 h = own_row ? WA(jj + c, jj) : make_double2(0.0, 0.0);
+      mine[4 * c + 2] = h.x;
+      mine[4 * c + 3] = h.y;
+    }
+  };
+  {
+    double* mine = red[rp];
+    rp ^= 1;
+    prepare(0, mine);
+    // the Frobenius norm rides along in the first reduction
+    __shared__ double s_fro[NWARP];
+    const double f = warp_sum(fro);
+    if (lane == 0) s_fro[warp] = f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < NWARP; ++w) sum += s_fro[w];
+      mine[4 * n] = sum;
+    }
+    team_reduce_vec(tm, mine, redo, 4 * n + 1);
+  }
   pc.lap(P.ctl, 8);
-  const double thr = QR_NULL_REL * sqrt(v[0]);
-  double sig2 = v[1];
-  double2 x0 = make_double2(v[2], v[3]);
+  const double thr = QR_NULL_REL * sqrt(redo[4 * n]);
   for (int j = 0; j < n; ++j) {
+    const double2 x0 = make_double2(redo[2], redo[3]);
+    const double sig2 = (x0.x * x0.x + x0.y * x0.y) + redo[0];
     const double sigma = sqrt(sig2);
     double tau = 0.0;
     double2 vh = make_double2(0, 0), alpha = make_double2(0, 0);
@@ -1199,86 +1377,59 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
       double2 ph = ax > 0.0 ? make_double2(x0.x / ax, x0.y / ax) : make_double2(1.0, 0.0);
       alpha = make_double2(-ph.x * sigma, -ph.y * sigma);
       vh = make_double2(x0.x - alpha.x, x0.y - alpha.y);
-      const double vn2 = sig2 - ax * ax + (vh.x * vh.x + vh.y * vh.y);
+      const double vn2 = redo[0] + (vh.x * vh.x + vh.y * vh.y);
       tau = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
     }
+    const int nk = n - j - 1;
     if (threadIdx.x == 0) {
       qs.tau[j] = tau;
       qs.shat[j] = tau > 0.0 ? sqrt(0.5 * tau) : 0.0;
       qs.vhead[j] = vh;
       qs.rdiag[j] = alpha;
     }
-    const int nk = n - j - 1;
-    const long long r0 = max(rb, (long long)j);  // own rows at or below the diagonal
-    const int nrr = (int)max(0LL, re - r0);
-    const double2* Vj = W + (long long)j * rows;
-    double nv[3] = {0, 0, 0};
     if (!null && nk > 0) {
-      // c_k = tau sum_{r >= j} conj(v_r) W[k][r], k > j: warp w takes columns w, w + NWARP, ...
-      // (four at a time), its lanes the CTA's rows
-      double* mine = red[rp];
-      rp ^= 1;
-      for (int k0 = warp; k0 < nk; k0 += 4 * NWARP) {
-        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (long long r = r0 + lane; r < re; r += 32) {
-          const double2 vr = (r == j) ? vh : Vj[r];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int k = k0 + q * NWARP;
-            if (k < nk) {
-              const double2 w = W[(long long)(j + 1 + k) * rows + r];
-              acc[2 * q] = fma(vr.x, w.x, fma(vr.y, w.y, acc[2 * q]));
-              acc[2 * q + 1] = fma(vr.x, w.y, fma(-vr.y, w.x, acc[2 * q + 1]));
-            }
-          }
-        }
-        warp_sum_n<8>(acc);
-        if (lane == 0) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int k = k0 + q * NWARP;
-            if (k < nk) {
-              mine[2 * k] = acc[2 * q];
-              mine[2 * k + 1] = acc[2 * q + 1];
-            }
-          }
-        }
+      // c_k = tau (d_k + conj(vh) h_k) for the trailing columns k = j+1 ..
+      for (int k = threadIdx.x; k < nk; k += NT) {
+        const int sl = 4 * (k + 1);
+        const double dr = redo[sl] + (vh.x * redo[sl + 2] + vh.y * redo[sl + 3]);
+        const double di = redo[sl + 1] + (vh.x * redo[sl + 3] - vh.y * redo[sl + 2]);
+        qs.coef[k] = make_double2(tau * dr, tau * di);
       }
-      team_reduce_vec(tm, mine, redo, 2 * nk);
-      // update the trailing columns on the own rows; gather the next column's reduction
+      __syncthreads();
+      // update the trailing columns on the own rows r >= j
+      const long long r0 = max(rb, (long long)j);
+      const int nrr = (int)max(0LL, re - r0);
       const float inv_nrr = nrr > 0 ? 1.0f / (float)nrr : 0.0f;
       for (int idx = threadIdx.x; idx < nk * nrr; idx += NT) {
         const int k = fdivu(idx, nrr, inv_nrr);
         const long long r = r0 + (idx - k * nrr);
-        const double2 vr = (r == j) ? vh : Vj[r];
-        const double2 ck = make_double2(tau * redo[2 * k], tau * redo[2 * k + 1]);
-        double2* wp = &W[(long long)(j + 1 + k) * rows + r];
+        const double2 vr = (r == j) ? vh : WA(j, r);
+        const double2 ck = qs.coef[k];
+        double2* wp = &WA(j + 1 + k, r);
         double2 w = *wp;
         w.x -= vr.x * ck.x - vr.y * ck.y;
         w.y -= vr.x * ck.y + vr.y * ck.x;
         *wp = w;
-        if (k == 0 && r >= j + 1) {
-          nv[0] = fma(w.x, w.x, fma(w.y, w.y, nv[0]));
-          if (r == j + 1) { nv[1] = w.x; nv[2] = w.y; }
-        }
       }
-      team_allreduce(tm, nv, 3);
-      sig2 = nv[0];
-      x0 = make_double2(nv[1], nv[2]);
-    } else if (nk > 0) {
-      // no reflection: the next column's reduction on unchanged data
-      const double2* Wn = W + (long long)(j + 1) * rows;
-      for (long long r = max(rb, (long long)j + 1) + threadIdx.x; r < re; r += NT) {
-        const double2 w = Wn[r];
-        nv[0] = fma(w.x, w.x, fma(w.y, w.y, nv[0]));
-        if (r == j + 1) { nv[1] = w.x; nv[2] = w.y; }
-      }
-      team_allreduce(tm, nv, 3);
-      sig2 = nv[0];
-      x0 = make_double2(nv[1], nv[2]);
+    }
+    if (nk > 0) {
+      __syncthreads();  // the updates (pair mapping) before the next column's dots (lane mapping)
+      double* mine = red[rp];
+      rp ^= 1;
+      prepare(j + 1, mine);
+      team_reduce_vec(tm, mine, redo, 4 * nk);
     }
   }
   __syncthreads();
+  if (in_smem) {  // rows < n to the global workspace (read across CTAs below)
+    const long long rt = min(re, (long long)n);
+    const int ntop = (int)max(0LL, rt - rb);
+    for (int idx = threadIdx.x; idx < n * ntop; idx += NT) {
+      const int c = idx / ntop;
+      const long long r = rb + (idx - c * ntop);
+      W[(long long)c * rows + r] = WA(c, r);
+    }
+  }
   pc.lap(P.ctl, 9);
   // Compact WY form Q = I - Vh T Vh^H, built from the unit-norm reflectors vh_j = v_j / |v_j|
   // (tau = 2): a column just above the null threshold has |v_j| ~ 1e-8 |M| and tau_j ~ 1e16,
@@ -1293,22 +1444,20 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
       const int a = pidx / n, b = pidx - (pidx / n) * n;
       double g0r = 0, g0i = 0, g1r = 0, g1i = 0;
       if (a <= b && qs.tau[a] != 0.0 && qs.tau[b] != 0.0) {
-        const double2* Va = W + (long long)a * rows;
-        const double2* Vb = W + (long long)b * rows;
         long long r = max(rb, (long long)b);
         for (; r + 1 < re; r += 2) {
-          const double2 va0 = (r == a) ? qs.vhead[a] : Va[r];
-          const double2 vb0 = (r == b) ? qs.vhead[b] : Vb[r];
-          const double2 va1 = Va[r + 1];
-          const double2 vb1 = (r + 1 == b) ? qs.vhead[b] : Vb[r + 1];
+          const double2 va0 = (r == a) ? qs.vhead[a] : WA(a, r);
+          const double2 vb0 = (r == b) ? qs.vhead[b] : WA(b, r);
+          const double2 va1 = WA(a, r + 1);
+          const double2 vb1 = (r + 1 == b) ? qs.vhead[b] : WA(b, r + 1);
           g0r = fma(va0.x, vb0.x, fma(va0.y, vb0.y, g0r));
           g0i = fma(va0.x, vb0.y, fma(-va0.y, vb0.x, g0i));
           g1r = fma(va1.x, vb1.x, fma(va1.y, vb1.y, g1r));
           g1i = fma(va1.x, vb1.y, fma(-va1.y, vb1.x, g1i));
         }
         if (r < re) {
-          const double2 va0 = (r == a) ? qs.vhead[a] : Va[r];
-          const double2 vb0 = (r == b) ? qs.vhead[b] : Vb[r];
+          const double2 va0 = (r == a) ? qs.vhead[a] : WA(a, r);
+          const double2 vb0 = (r == b) ? qs.vhead[b] : WA(b, r);
           g0r = fma(va0.x, vb0.x, fma(va0.y, vb0.y, g0r));
           g0i = fma(va0.x, vb0.y, fma(-va0.y, vb0.x, g0i));
         }
@@ -1392,7 +1541,7 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     double qre = (r == c) ? 1.0 : 0.0, qim = 0.0;
     for (int j = 0; j <= jmax; ++j) {
       if (qs.tau[j] == 0.0) continue;
-      const double2 vr = (r == j) ? qs.vhead[j] : W[(long long)j * rows + r];
+      const double2 vr = (r == j) ? qs.vhead[j] : WA(j, r);
       const double2 z = Z[j * TTNS_MAX_D + c];
       qre -= vr.x * z.x - vr.y * z.y;
       qim -= vr.x * z.y + vr.y * z.x;

@@ -66,7 +66,8 @@ class Counters(C.Structure):
     _fields_ = [("krylov_iters", C.c_longlong), ("applies", C.c_longlong), ("contraction_flops", C.c_double),
                 ("not_converged", C.c_longlong), ("steps", C.c_longlong), ("op_seconds", (C.c_double * 2) * 6),
                 ("op_count", (C.c_longlong * 2) * 6), ("expm_phase_seconds", C.c_double * 8),
-                ("qr_phase_seconds", C.c_double * 8)]
+                ("qr_phase_seconds", C.c_double * 8), ("expm_phase_seconds_grid", C.c_double * 8),
+                ("qr_phase_seconds_grid", C.c_double * 8)]
 
 
 _lib = None
@@ -305,9 +306,13 @@ class Tree:
         phases = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm"],
                           [c.expm_phase_seconds[k] for k in range(7)]))
         qr = dict(zip(["copy_norm", "columns", "gram", "T_Z", "write_Q"], [c.qr_phase_seconds[k] for k in range(5)]))
+        phases_g = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm"],
+                            [c.expm_phase_seconds_grid[k] for k in range(7)]))
+        qr_g = dict(zip(["copy_norm", "columns", "gram", "T_Z", "write_Q"],
+                        [c.qr_phase_seconds_grid[k] for k in range(5)]))
         return {"krylov_iters": c.krylov_iters, "applies": c.applies, "contraction_flops": c.contraction_flops,
                 "not_converged": c.not_converged, "steps": c.steps, "profile": prof, "expm_phases": phases,
-                "qr_phases": qr}
+                "qr_phases": qr, "expm_phases_grid": phases_g, "qr_phases_grid": qr_g}
 
     def n_nodes(self, k: int = 0) -> int:
         n = C.c_int()
