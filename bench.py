@@ -29,6 +29,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
+# DRAM bytes (read + write) of one k_sweep launch (one headline step), from the ncu DRAM
+# counters of this kernel build: profiles/k_sweep_dram_sf_5state_4x20.md
+KSWEEP_DRAM_BYTES_PER_STEP = 620.07e6
+
 METRIC = "ttns_sweeps_per_s"
 UNIT = "sweeps/s"
 WORKLOAD = "sf_5state_4x20_d10_D20"
@@ -255,7 +259,9 @@ def main():
     fp32_peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12  # FP32 FMA units x 2 flops x max SM clock
     achieved = flops / (total_ms * 1e-3) / 1e12 / world if total_ms > 0 else 0.0
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak_tflops, "traffic": None,
+            "frac": achieved / fp32_peak_tflops,
+            "traffic": KSWEEP_DRAM_BYTES_PER_STEP if args.workload == WORKLOAD else None,
+            "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
             "kernel": "k_sweep (whole sweep, one persistent launch)",
             "peak_note": "FP32 SIMT FMA peak from unit counts and max clock (152 SMs x 128 lanes x 2 x 2.07 GHz)"}
 

@@ -182,8 +182,9 @@ typedef struct {
    * factors of two-factor terms, 2 apply + alpha reduction, 3 recurrence + beta
    * reduction, 4 small exponential / convergence, 5 final combination, 6 norm */
   double expm_phase_seconds[8];
-  /* phases of the cluster-team QRs: 0 copy + norm, 1 column loop, 2 Gram of the
-   * reflectors, 3 T and Z, 4 Q and R written back */
+  /* phases of the cluster-team QRs: 0 copy + norm, 1 column loop (its team reductions),
+   * 2 Gram of the reflectors, 3 T and Z, 4 Q and R written back, and inside the column
+   * loop 5 reflector and coefficients, 6 trailing update, 7 dots for the next column */
   double qr_phase_seconds[8];
   /* the same two breakdowns for the grid-team (whole-GPU) operations */
   double expm_phase_seconds_grid[8];

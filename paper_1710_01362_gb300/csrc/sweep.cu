@@ -656,9 +656,15 @@ __device__ void team_reduce_vec(Team& tm, const double* mine, double* out, int n
     cg::cluster_group cl = cg::this_cluster();
     cl.sync();
     for (int k = threadIdx.x; k < nval; k += NT) {
-      double s = 0.0;
-      for (int r = 0; r < tm.size; ++r) s += *cl.map_shared_rank(mine + k, r);
-      out[k] = s;
+      // the 16 peers' values loaded together, then added in a fixed tree (depth 4)
+      double a[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) a[r] = r < tm.size ? *cl.map_shared_rank(mine + k, r) : 0.0;
+#pragma unroll
+      for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+        for (int r = 0; r < w; ++r) a[r] += a[r + w];
+      out[k] = a[0];
     }
   } else {
     double* buf = team_partials(tm);
@@ -666,7 +672,16 @@ __device__ void team_reduce_vec(Team& tm, const double* mine, double* out, int n
     team_sync(tm);
     for (int k = threadIdx.x; k < nval; k += NT) {
       double s = 0.0;
-      for (int r = 0; r < tm.size; ++r) s += buf[(long long)r * nval + k];
+      for (int r0 = 0; r0 < tm.size; r0 += 16) {  // blocks of 16 ranks, each added in a tree
+        double a[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) a[r] = r0 + r < tm.size ? buf[(long long)(r0 + r) * nval + k] : 0.0;
+#pragma unroll
+        for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+          for (int r = 0; r < w; ++r) a[r] += a[r + w];
+        s += a[0];
+      }
       out[k] = s;
     }
     tm.parity ^= 1;
@@ -1278,10 +1293,6 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   double2* W = work;  // column-major: W[c * rows + r]
   double2* Rout = P.pool + P.trees[I.tree].bond_off;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // per-CTA scratch for the small matrices G (Gram of V), T, Z
-  double2* G = P.cta_scratch + (long long)blockIdx.x * P.cta_scratch_stride;
-  double2* Tm = G + TTNS_MAX_D * TTNS_MAX_D;
-  double2* Z = Tm + TTNS_MAX_D * TTNS_MAX_D;
   const long long chunk = (rows + tm.size - 1) / tm.size;
   const long long rb = min(rows, (long long)tm.rank * chunk);
   const long long re = min(rows, rb + chunk);
@@ -1301,6 +1312,15 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   const long long ldw = in_smem ? chunk : rows;
   const long long roff = in_smem ? rb : 0;
   auto WA = [&](int c, long long r) -> double2& { return Wl[(long long)c * ldw + (r - roff)]; };
+  // the small matrices G (Gram of the reflectors), T and Z (n x n, row stride ldg): after the
+  // rows in shared memory when they fit there too, else in the per-CTA global scratch
+  const long long g_off = (ws_off + (in_smem ? (long long)n * chunk * (long long)sizeof(double2) : 0) + 15) & ~15LL;
+  const bool g_smem = g_off + 3LL * n * n * (long long)sizeof(double2) <= P.smem_bytes;
+  const int ldg = g_smem ? n : TTNS_MAX_D;
+  double2* G = g_smem ? reinterpret_cast<double2*>(dyn_smem + g_off)
+                      : P.cta_scratch + (long long)blockIdx.x * P.cta_scratch_stride;
+  double2* Tm = G + ldg * ldg;
+  double2* Z = Tm + ldg * ldg;
   // copy into the column-major workspace; the Frobenius norm sets the null threshold
   double fro = 0.0;
   for (int idx = threadIdx.x; idx < n * nr; idx += NT) {
@@ -1316,28 +1336,75 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   //   d_c = sum_r conj(W[j][r]) W[c][r]   and   h_c = W[c][j]  (row j: its owner only),
   // in slots [4 (c - j) .. 4 (c - j) + 4).  Then sigma_j^2 = |h_j|^2 + d_j, x0 = h_j, and
   // c_k = tau (d_k + conj(vh) h_k) is v^H W[k] with the head of v replaced by vh.
+  // Products and sums are packed so that few FP64 instructions run with idle lanes: when
+  // the CTA's rows below jj number at most 32, one thread forms each (column, row) product
+  // into shared memory and the per-column sums are fixed trees; for more rows, warps take
+  // columns four at a time with a transposing butterfly.
+  // product scratch (n x 32 complex) after G, T, Z
+  const long long p_off = (g_off + (g_smem ? 3LL * n * n * (long long)sizeof(double2) : 0) + 15) & ~15LL;
+  const bool p_smem = g_smem && p_off + 32LL * n * (long long)sizeof(double2) <= P.smem_bytes;
+  double2* const prod = reinterpret_cast<double2*>(dyn_smem + p_off);
   auto prepare = [&](int jj, double* mine) {
     const int nc = n - jj;
     const long long r1 = max(rb, (long long)jj + 1);
-    for (int c0 = 0; c0 < nc; c0 += 4 * NWARP) {
-      double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      for (long long r = r1 + lane; r < re; r += 32) {
-        const double2 vr = WA(jj, r);
+    const int nrw = (int)max(0LL, re - r1);  // own rows strictly below row jj
+    if (p_smem && chunk <= 32) {  // the same branch on every CTA (chunk is uniform)
+      // prod[c * 32 + r] = conj(v_r) W[jj + c][r], zero-padded to 32 rows
+      for (int idx = threadIdx.x; idx < nc * 32; idx += NT) {
+        const int c = idx >> 5, rr = idx & 31;
+        double2 p = make_double2(0.0, 0.0);
+        if (rr < nrw) {
+          const long long r = r1 + rr;
+          const double2 vr = WA(jj, r), w = WA(jj + c, r);
+          p = make_double2(fma(vr.x, w.x, vr.y * w.y), fma(vr.x, w.y, -vr.y * w.x));
+        }
+        prod[idx] = p;
+      }
+      __syncthreads();
+      // per column: 8 threads add 4 rows each, then a fixed tree over the 8 partials (the
+      // trip count is rounded to whole warps so that every lane takes part in the shuffles)
+      const int ntask = nc * 8;
+      for (int idx = threadIdx.x; idx < ((ntask + 31) & ~31); idx += NT) {
+        const bool on = idx < ntask;
+        const int c = idx >> 3, g = idx & 7;
+        double sr = 0.0, si = 0.0;
+        if (on) {
+          const double2* pc2 = prod + c * 32 + g;
+          const double2 s0 = pc2[0], s1 = pc2[8], s2 = pc2[16], s3 = pc2[24];
+          sr = (s0.x + s1.x) + (s2.x + s3.x);
+          si = (s0.y + s1.y) + (s2.y + s3.y);
+        }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int c = c0 + warp + q * NWARP;
-          if (c < nc) {
-            const double2 w = WA(jj + c, r);
-            acc[2 * q] = fma(vr.x, w.x, fma(vr.y, w.y, acc[2 * q]));
-            acc[2 * q + 1] = fma(vr.x, w.y, fma(-vr.y, w.x, acc[2 * q + 1]));
-          }
+        for (int o = 4; o >= 1; o >>= 1) {  // within the aligned group of 8 lanes
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (on && g == 0) {
+          mine[4 * c] = sr;
+          mine[4 * c + 1] = si;
         }
       }
-      const double t = warp_reduce_t<8>(acc);
-      if ((lane & 3) == 0) {
-        const int vid = warp_reduce_vid<8>(lane);
-        const int c = c0 + warp + (vid >> 1) * NWARP;
-        if (c < nc) mine[4 * c + (vid & 1)] = t;
+    } else {
+      for (int c0 = 0; c0 < nc; c0 += 4 * NWARP) {
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (long long r = r1 + lane; r < re; r += 32) {
+          const double2 vr = WA(jj, r);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = c0 + warp + q * NWARP;
+            if (c < nc) {
+              const double2 w = WA(jj + c, r);
+              acc[2 * q] = fma(vr.x, w.x, fma(vr.y, w.y, acc[2 * q]));
+              acc[2 * q + 1] = fma(vr.x, w.y, fma(-vr.y, w.x, acc[2 * q + 1]));
+            }
+          }
+        }
+        const double t = warp_reduce_t<8>(acc);
+        if ((lane & 3) == 0) {
+          const int vid = warp_reduce_vid<8>(lane);
+          const int c = c0 + warp + (vid >> 1) * NWARP;
+          if (c < nc) mine[4 * c + (vid & 1)] = t;
+        }
       }
     }
     const bool own_row = rb <= jj && jj < re;
@@ -1366,24 +1433,35 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   pc.lap(P.ctl, 8);
   const double thr = QR_NULL_REL * sqrt(redo[4 * n]);
   for (int j = 0; j < n; ++j) {
+    // reflector of column j: alpha = -phase(x0) sigma, vh = x0 - alpha = x0 (1 + sigma / |x0|),
+    // |vh| = |x0| + sigma, |v|^2 = d_j + |vh|^2, tau = 2 / |v|^2.  Written so that the FP64
+    // square roots and divisions (long dependent sequences on this part) overlap.
     const double2 x0 = make_double2(redo[2], redo[3]);
-    const double sig2 = (x0.x * x0.x + x0.y * x0.y) + redo[0];
-    const double sigma = sqrt(sig2);
-    double tau = 0.0;
+    const double ax2 = x0.x * x0.x + x0.y * x0.y;
+    const double sigma = sqrt(ax2 + redo[0]);
+    const double ax = sqrt(ax2);
+    double tau = 0.0, shat = 0.0;
     double2 vh = make_double2(0, 0), alpha = make_double2(0, 0);
     const bool null = !(sigma > thr);
     if (!null) {
-      const double ax = sqrt(x0.x * x0.x + x0.y * x0.y);
-      double2 ph = ax > 0.0 ? make_double2(x0.x / ax, x0.y / ax) : make_double2(1.0, 0.0);
-      alpha = make_double2(-ph.x * sigma, -ph.y * sigma);
-      vh = make_double2(x0.x - alpha.x, x0.y - alpha.y);
-      const double vn2 = redo[0] + (vh.x * vh.x + vh.y * vh.y);
-      tau = vn2 > 0.0 ? 2.0 / vn2 : 0.0;
+      const double inv_ax = ax > 0.0 ? 1.0 / ax : 0.0;
+      const double hv = ax + sigma;
+      const double vn2 = redo[0] + hv * hv;
+      tau = 2.0 / vn2;
+      shat = rsqrt(vn2);
+      if (ax > 0.0) {
+        const double f = sigma * inv_ax;
+        alpha = make_double2(-f * x0.x, -f * x0.y);
+        vh = make_double2(x0.x + f * x0.x, x0.y + f * x0.y);
+      } else {
+        alpha = make_double2(-sigma, 0.0);
+        vh = make_double2(sigma, 0.0);
+      }
     }
     const int nk = n - j - 1;
     if (threadIdx.x == 0) {
       qs.tau[j] = tau;
-      qs.shat[j] = tau > 0.0 ? sqrt(0.5 * tau) : 0.0;
+      qs.shat[j] = shat;
       qs.vhead[j] = vh;
       qs.rdiag[j] = alpha;
     }
@@ -1396,6 +1474,7 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
         qs.coef[k] = make_double2(tau * dr, tau * di);
       }
       __syncthreads();
+      pc.lap(P.ctl, 13);
       // update the trailing columns on the own rows r >= j
       const long long r0 = max(rb, (long long)j);
       const int nrr = (int)max(0LL, re - r0);
@@ -1414,10 +1493,13 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     }
     if (nk > 0) {
       __syncthreads();  // the updates (pair mapping) before the next column's dots (lane mapping)
+      pc.lap(P.ctl, 14);
       double* mine = red[rp];
       rp ^= 1;
       prepare(j + 1, mine);
+      pc.lap(P.ctl, 15);
       team_reduce_vec(tm, mine, redo, 4 * nk);
+      pc.lap(P.ctl, 9);
     }
   }
   __syncthreads();
@@ -1471,30 +1553,38 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
       if (a > b) continue;
       const double sab = qs.shat[a] * qs.shat[b];
       const double gr = sab * redo[2 * pidx], gi = sab * redo[2 * pidx + 1];
-      G[a * TTNS_MAX_D + b] = make_double2(gr, gi);
-      G[b * TTNS_MAX_D + a] = make_double2(gr, -gi);
+      G[a * ldg + b] = make_double2(gr, gi);
+      G[b * ldg + a] = make_double2(gr, -gi);
     }
     __syncthreads();
   }
   pc.lap(P.ctl, 10);
   // T (upper triangular): T[j][j] = 2, T[0:j, j] = -2 T[0:j, 0:j] G[0:j, j] (rows and columns
   // of identity reflectors stay zero)
-  for (int idx = threadIdx.x; idx < n * n; idx += NT) Tm[idx / n * TTNS_MAX_D + idx % n] = make_double2(0, 0);
+  for (int idx = threadIdx.x; idx < n * n; idx += NT) Tm[idx / n * ldg + idx % n] = make_double2(0, 0);
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     const double tj = qs.tau[j] != 0.0 ? 2.0 : 0.0;
     if (threadIdx.x < j && tj != 0.0) {
       const int i = threadIdx.x;
-      double sr = 0, si = 0;
-      for (int k = i; k < j; ++k) {
-        const double2 t = Tm[i * TTNS_MAX_D + k];
-        const double2 g = G[k * TTNS_MAX_D + j];
-        sr += t.x * g.x - t.y * g.y;
-        si += t.x * g.y + t.y * g.x;
+      double sr0 = 0, si0 = 0, sr1 = 0, si1 = 0;  // two chains (FP64 latency)
+      int k = i;
+      for (; k + 1 < j; k += 2) {
+        const double2 t0 = Tm[i * ldg + k], g0 = G[k * ldg + j];
+        const double2 t1 = Tm[i * ldg + k + 1], g1 = G[(k + 1) * ldg + j];
+        sr0 = fma(t0.x, g0.x, fma(-t0.y, g0.y, sr0));
+        si0 = fma(t0.x, g0.y, fma(t0.y, g0.x, si0));
+        sr1 = fma(t1.x, g1.x, fma(-t1.y, g1.y, sr1));
+        si1 = fma(t1.x, g1.y, fma(t1.y, g1.x, si1));
       }
-      Tm[i * TTNS_MAX_D + j] = make_double2(-tj * sr, -tj * si);
+      if (k < j) {
+        const double2 t0 = Tm[i * ldg + k], g0 = G[k * ldg + j];
+        sr0 = fma(t0.x, g0.x, fma(-t0.y, g0.y, sr0));
+        si0 = fma(t0.x, g0.y, fma(t0.y, g0.x, si0));
+      }
+      Tm[i * ldg + j] = make_double2(-tj * (sr0 + sr1), -tj * (si0 + si1));
     }
-    if (threadIdx.x == 0) Tm[j * TTNS_MAX_D + j] = make_double2(tj, 0.0);
+    if (threadIdx.x == 0) Tm[j * ldg + j] = make_double2(tj, 0.0);
     __syncthreads();
   }
   // Z[j][c] = shat_j sum_{j <= i <= c} T[j][i] shat_i conj(V[c][i]), so that
@@ -1504,14 +1594,14 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     double zr = 0, zi = 0;
     for (int i = j; i <= c; ++i) {
       if (qs.tau[i] == 0.0) continue;
-      const double2 t = Tm[j * TTNS_MAX_D + i];
+      const double2 t = Tm[j * ldg + i];
       const double2 v = (c == i) ? qs.vhead[i] : W[(long long)i * rows + c];
       const double si = qs.shat[i];
       const double2 vci = make_double2(si * v.x, si * v.y);
       zr += t.x * vci.x + t.y * vci.y;
       zi += t.y * vci.x - t.x * vci.y;
     }
-    Z[j * TTNS_MAX_D + c] = make_double2(qs.shat[j] * zr, qs.shat[j] * zi);
+    Z[j * ldg + c] = make_double2(qs.shat[j] * zr, qs.shat[j] * zi);
   }
   pc.lap(P.ctl, 11);
   // phases of the diagonal of R
@@ -1542,7 +1632,7 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     for (int j = 0; j <= jmax; ++j) {
       if (qs.tau[j] == 0.0) continue;
       const double2 vr = (r == j) ? qs.vhead[j] : WA(j, r);
-      const double2 z = Z[j * TTNS_MAX_D + c];
+      const double2 z = Z[j * ldg + c];
       qre -= vr.x * z.x - vr.y * z.y;
       qim -= vr.x * z.y + vr.y * z.x;
     }

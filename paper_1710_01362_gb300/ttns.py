@@ -305,11 +305,11 @@ class Tree:
                     prof[f"{names[op]}_{team}"] = (c.op_seconds[op][k], c.op_count[op][k])
         phases = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm"],
                           [c.expm_phase_seconds[k] for k in range(7)]))
-        qr = dict(zip(["copy_norm", "columns", "gram", "T_Z", "write_Q"], [c.qr_phase_seconds[k] for k in range(5)]))
+        qr_names = ["copy_norm", "columns", "gram", "T_Z", "write_Q", "col_reflector", "col_update", "col_dots"]
+        qr = dict(zip(qr_names, [c.qr_phase_seconds[k] for k in range(8)]))
         phases_g = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm"],
                             [c.expm_phase_seconds_grid[k] for k in range(7)]))
-        qr_g = dict(zip(["copy_norm", "columns", "gram", "T_Z", "write_Q"],
-                        [c.qr_phase_seconds_grid[k] for k in range(5)]))
+        qr_g = dict(zip(qr_names, [c.qr_phase_seconds_grid[k] for k in range(8)]))
         return {"krylov_iters": c.krylov_iters, "applies": c.applies, "contraction_flops": c.contraction_flops,
                 "not_converged": c.not_converged, "steps": c.steps, "profile": prof, "expm_phases": phases,
                 "qr_phases": qr, "expm_phases_grid": phases_g, "qr_phases_grid": qr_g}
