@@ -29,9 +29,9 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
-# DRAM bytes (read + write) of one k_sweep launch (one headline step), from the ncu DRAM
-# counters of this kernel build: profiles/k_sweep_dram_sf_5state_4x20.md
-KSWEEP_DRAM_BYTES_PER_STEP = 620.07e6
+# DRAM bytes (read + write) of one k_sweep launch (one headline step), from one ncu capture
+# of dram__bytes_read.sum + dram__bytes_write.sum for this kernel build (mean of two launches)
+KSWEEP_DRAM_BYTES_PER_STEP = 664.03e6
 
 METRIC = "ttns_sweeps_per_s"
 UNIT = "sweeps/s"

@@ -379,8 +379,17 @@ __device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& 
     // converted once here, so that the contractions read compute-type operands (a
     // double -> float conversion per use would run on the FP64 pipe)
     float2* sm = reinterpret_cast<float2*>(dyn_smem);
-    for (int k = threadIdx.x; k < os.a_n; k += NT) sm[k] = cvt<float>(__ldg(P.pool + os.a_off + k));
-    for (int k = threadIdx.x; k < os.b_n; k += NT) sm[os.a_n + k] = cvt<float>(__ldg(P.pool + os.b_off + k));
+    const int nt = os.a_n + os.b_n;  // the two regions back to back, four loads in flight per thread
+    auto src = [&](int k) -> const double2* { return k < os.a_n ? P.pool + os.a_off + k : P.pool + os.b_off + (k - os.a_n); };
+    int k = threadIdx.x;
+    for (; k + 3 * NT < nt; k += 4 * NT) {
+      const double2 v0 = __ldg(src(k)), v1 = __ldg(src(k + NT)), v2 = __ldg(src(k + 2 * NT)), v3 = __ldg(src(k + 3 * NT));
+      sm[k] = cvt<float>(v0);
+      sm[k + NT] = cvt<float>(v1);
+      sm[k + 2 * NT] = cvt<float>(v2);
+      sm[k + 3 * NT] = cvt<float>(v3);
+    }
+    for (; k < nt; k += NT) sm[k] = cvt<float>(__ldg(src(k)));
   }
   __syncthreads();
 }
@@ -1056,6 +1065,137 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
   return true;
 }
 
+// Tiled apply for grid-team nodes too large for shared memory.  The node (legs 0..nl-1, the
+// last one physical) is covered twice by tiles:
+//   pass A: tiles over legs h..nl-1 (contiguous blocks), one per index of legs 0..h-1;
+//   pass B: tiles over legs 0..h-1 and nl-1, one per index of legs h..nl-2;
+// with h = (nl - 1) / 2.  A term is computed in the pass whose tile holds all its legs, from
+// the tile of the input vector staged in shared memory (every element of a tile is read by
+// D of its neighbours along a leg: this replaces strided L2 reads).  Pass A writes its sum,
+// pass B adds its terms to it.  Two-stage terms, or a term with legs in neither tile, keep
+// the element-wise apply.
+struct TiledApply {
+  NodeDesc ta, tb;                  // the tile tensors of the two passes
+  int h;
+  int lmapA[TTNS_MAX_LEGS], lmapB[TTNS_MAX_LEGS];  // tile leg of each node leg (-1: none)
+  int nst[TTNS_MAX_LEGS];           // node strides of the tile-B legs 0..h-1
+  int bdims[TTNS_MAX_LEGS], bst[TTNS_MAX_LEGS];    // legs h..nl-2: dims and node strides
+  int nb;                           // number of such legs
+  int nta, ntb;
+  unsigned long long inB;           // bit t: term t is computed in pass B
+  int ok;
+};
+__shared__ TiledApply s_tp;
+
+__device__ void tiled_plan(const NodeDesc& nd, const OpStage& os, const TermList& L, TiledApply& tp) {
+  const int nl = nd.nl, h = (nl - 1) / 2;
+  tp.ok = nl >= 3 && h >= 1 && L.n2 == 0 && L.count <= 64;
+  if (!tp.ok) return;
+  tp.h = h;
+  NodeDesc& a = tp.ta;
+  a.nl = nl - h;
+  for (int q = 0; q < a.nl; ++q) {
+    a.dims[q] = nd.dims[h + q];
+    a.strides[q] = nd.strides[h + q];
+  }
+  a.size = nd.strides[h - 1];
+  NodeDesc& b = tp.tb;
+  b.nl = h + 1;
+  for (int q = 0; q < h; ++q) b.dims[q] = nd.dims[q];
+  b.dims[h] = nd.dims[nl - 1];
+  b.strides[h] = 1;
+  for (int q = h - 1; q >= 0; --q) b.strides[q] = b.strides[q + 1] * b.dims[q + 1];
+  b.size = b.strides[0] * b.dims[0];
+  for (int q = 0; q < a.nl; ++q) {
+    a.inv_dims[q] = 1.0f / (float)a.dims[q];
+    a.inv_strides[q] = 1.0f / (float)a.strides[q];
+  }
+  for (int q = 0; q < b.nl; ++q) {
+    b.inv_dims[q] = 1.0f / (float)b.dims[q];
+    b.inv_strides[q] = 1.0f / (float)b.strides[q];
+  }
+  for (int l = 0; l < TTNS_MAX_LEGS; ++l) {
+    tp.lmapA[l] = (l >= h && l < nl) ? l - h : -1;
+    tp.lmapB[l] = l < h ? l : (l == nl - 1 ? h : -1);
+  }
+  for (int q = 0; q < h; ++q) tp.nst[q] = nd.strides[q];
+  tp.nb = nl - 1 - h;
+  for (int q = 0; q < tp.nb; ++q) {
+    tp.bdims[q] = nd.dims[h + q];
+    tp.bst[q] = nd.strides[h + q];
+  }
+  tp.nta = (int)(nd.size / a.size);
+  tp.ntb = (int)(nd.size / b.size);
+  tp.inB = 0ull;
+  for (int t = 0; t < L.count; ++t) {
+    const Term& tt = os.terms[t];
+    bool allA = true, allB = true;
+    for (int k = 0; k < tt.nf; ++k) {
+      allA = allA && tp.lmapA[tt.f[k].leg] >= 0;
+      allB = allB && tp.lmapB[tt.f[k].leg] >= 0;
+    }
+    if (!allA) {
+      if (allB) tp.inB |= 1ull << t;
+      else tp.ok = 0;
+    }
+  }
+}
+
+// One pass over this CTA's tiles; emit(global index, sum of the pass's terms at it).
+template <typename T, typename F>
+__device__ void tiled_pass(const KernelParams& P, Team& tm, const TiledApply& tp, const OpStage& os,
+                           const TermList& L, const typename C2<T>::t* xin, typename C2<T>::t* xt, int pass,
+                           F&& emit) {
+  using V = typename C2<T>::t;
+  const NodeDesc& td = pass ? tp.tb : tp.ta;
+  const int* lmap = pass ? tp.lmapB : tp.lmapA;
+  const int ntiles = pass ? tp.ntb : tp.nta;
+  const int TT = td.size;
+  const int h = tp.h;
+  auto gidx = [&](long long base, int e) -> long long {
+    if (!pass) return base + e;
+    long long g = base;
+    int rem = e;
+    for (int q = 0; q < h; ++q) {
+      const int iq = fdivu(rem, td.strides[q], td.inv_strides[q]);
+      rem -= iq * td.strides[q];
+      g += (long long)iq * tp.nst[q];
+    }
+    return g + rem;  // the physical leg has node stride 1
+  };
+  for (int tile = tm.rank; tile < ntiles; tile += tm.size) {
+    long long base;
+    if (!pass) {
+      base = (long long)tile * TT;
+    } else {
+      base = 0;
+      int rem = tile;
+      for (int q = tp.nb - 1; q >= 0; --q) {
+        const int iq = rem % tp.bdims[q];
+        rem /= tp.bdims[q];
+        base += (long long)iq * tp.bst[q];
+      }
+    }
+    __syncthreads();  // the previous tile's reads are done
+    for (int e = threadIdx.x; e < TT; e += NT) xt[e] = xin[gidx(base, e)];
+    __syncthreads();
+    for (int e = threadIdx.x; e < TT; e += NT) {
+      V acc;
+      acc.x = acc.y = (T)0;
+      for (int t = 0; t < L.count; ++t) {
+        if ((int)((tp.inB >> t) & 1ull) != pass) continue;
+        Term tt = os.terms[t];
+        tt.f[0].leg = lmap[tt.f[0].leg];
+        if (tt.nf == 2) tt.f[1].leg = lmap[tt.f[1].leg];
+        const V a = tt.nf == 1 ? factor_dot<T>(P, td, tt.f[0], os, xt, e) : direct_dot<T>(P, td, tt, os, xt, e);
+        acc.x += a.x;
+        acc.y += a.y;
+      }
+      emit(gidx(base, e), acc);
+    }
+  }
+}
+
 template <typename T>
 __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2* work, double tau) {
   KrylovShared& ks = s_ks;
@@ -1079,6 +1219,18 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
   constexpr bool kShadow = !std::is_same<T, double>::value;
   V* xf = reinterpret_cast<V*>(work + (long long)(P.mmax + P.n_tmp) * kv);
   const bool shadow = kShadow && xs == nullptr;
+  // tiled apply for a grid-team node that does not fit in shared memory
+  TiledApply& tp = s_tp;
+  V* xt = nullptr;
+  bool tiled = false;
+  if (tm.kind == TEAM_GRID && xs == nullptr) {
+    if (threadIdx.x == 0) tiled_plan(nd, os, L, tp);
+    __syncthreads();
+    if (tp.ok) {
+      xt = vec_smem<T>(P, os, tp.ta.size > tp.tb.size ? tp.ta.size : tp.tb.size);
+      tiled = xt != nullptr;  // the same on every CTA
+    }
+  }
   pc.lap(P.ctl, 0);
   // exp(-i s H): s = time / hbar with the op's sign.  If the Krylov space of dimension
   // mmax does not reach the tolerance for the remaining time, the largest s / 2^k that
@@ -1132,8 +1284,7 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
       // alpha_j and beta_{j+1}, as in the cluster-resident form)
       const bool mixed = P.precision != 0;
       double part[3] = {0.0, 0.0, 0.0};
-      for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) {
-        const auto a = apply_stage2_at<T>(P, nd, xin, L, tmp, kv, idx, os);
+      auto recur = [&](long long idx, V a) {  // w = s_j H K_j - beta_j q_{j-1} at idx, and the dots
         const double2 kj = Kj[idx];
         double wr = sj * (double)a.x, wi = sj * (double)a.y;
         if (j > 0) {
@@ -1147,6 +1298,19 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
           part[1] = fma(wr, wr, fma(wi, wi, part[1]));
           part[2] = fma(kj.x, kj.x, fma(kj.y, kj.y, part[2]));
         }
+      };
+      if (tiled) {
+        V* y = tmp;  // pass A sums (no two-stage terms, so the temporaries are free)
+        tiled_pass<T>(P, tm, tp, os, L, xin, xt, 0, [&](long long g, V acc) { y[g] = acc; });
+        team_sync(tm);
+        tiled_pass<T>(P, tm, tp, os, L, xin, xt, 1, [&](long long g, V acc) {
+          V a = y[g];
+          a.x += acc.x;
+          a.y += acc.y;
+          recur(g, a);
+        });
+      } else {
+        for (long long idx = tm.gtid(); idx < N; idx += tm.nthr()) recur(idx, apply_stage2_at<T>(P, nd, xin, L, tmp, kv, idx, os));
       }
       team_allreduce(tm, part, mixed ? 3 : 1);
       pc.lap(P.ctl, 2);
