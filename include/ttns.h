@@ -137,6 +137,17 @@ typedef struct {
 } ttns_plan_info;
 ttns_status ttns_plan(int n_trees, const ttns_problem* problems, const ttns_options* opt, ttns_plan_info* info);
 
+/* Autotuner of the team shape (the number of CTAs per cluster team; in batched mode this
+ * sets how many trees advance concurrently).  For each candidate (n_candidates == 0: 16, 8
+ * and 4), builds the tree set with *opt and that cluster size, runs one warm-up step of
+ * length dt_fs and times one step with CUDA events, then frees it.  Writes the fastest
+ * candidate to *best_cluster_ctas (and its seconds per step when best_seconds_per_step is
+ * not NULL); pass it as ttns_options.cluster_ctas to the real build.  Candidates must be in
+ * 1..16.  TTNS_E_CUDA when no candidate could run.  Uses the GPU; blocks. */
+ttns_status ttns_autotune(int n_trees, const ttns_problem* problems, const ttns_options* opt, double dt_fs,
+                          int n_candidates, const int* candidates, int* best_cluster_ctas,
+                          double* best_seconds_per_step);
+
 /* Advances every tree by n_steps symmetric one-site TDVP steps of length dt_fs
  * (S(dt/2) followed by its adjoint S*(dt/2)).  Asynchronous on the tree's
  * stream; device-side failures are reported by the next synchronising call. */

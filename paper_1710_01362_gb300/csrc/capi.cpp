@@ -466,6 +466,58 @@ static ttns_status build(int n_trees, const ttns_problem* probs, const ttns_opti
   return TTNS_OK;
 }
 
+// Autotuner of the team shape: for each candidate number of CTAs per cluster team, build the
+// same tree set, run one warm-up step and time one step with CUDA events on the options'
+// stream, free it; report the fastest.  The state evolves differently only by rounding, so
+// any candidate gives a valid run; the choice is purely a performance one.
+extern "C" ttns_status ttns_autotune(int n_trees, const ttns_problem* problems, const ttns_options* opt, double dt_fs,
+                                     int n_candidates, const int* candidates, int* best_cluster_ctas,
+                                     double* best_seconds_per_step) {
+  if (!best_cluster_ctas) return fail(TTNS_E_INVALID, "best_cluster_ctas is NULL");
+  if (!std::isfinite(dt_fs) || dt_fs == 0.0) return fail(TTNS_E_INVALID, "dt must be finite and nonzero");
+  static const int kDefault[3] = {16, 8, 4};
+  if (n_candidates < 0 || (n_candidates > 0 && !candidates)) return fail(TTNS_E_INVALID, "bad candidate list");
+  const int nc = n_candidates > 0 ? n_candidates : 3;
+  const int* cand = n_candidates > 0 ? candidates : kDefault;
+  for (int k = 0; k < nc; ++k)
+    if (cand[k] < 1 || cand[k] > 16) return fail(TTNS_E_INVALID, "cluster candidates must be in 1..16");
+  ttns_options base{};
+  if (opt) base = *opt;
+  base.record = 0;
+  base.profile = 0;
+  int best = 0;
+  double best_s = 0.0;
+  std::string last_err;
+  for (int k = 0; k < nc; ++k) {
+    ttns_options o = base;
+    o.cluster_ctas = cand[k];
+    ttns_tree* t = nullptr;
+    if (build(n_trees, problems, &o, &t) != TTNS_OK) {
+      last_err = g_err;
+      continue;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float ms = -1.0f;
+    bool ok = ttns_step(t, dt_fs, 1) == TTNS_OK && ttns_sync(t) == TTNS_OK;
+    ok = ok && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+    ok = ok && cudaEventRecord(e0, t->stream) == cudaSuccess && ttns_step(t, dt_fs, 1) == TTNS_OK &&
+         cudaEventRecord(e1, t->stream) == cudaSuccess && ttns_sync(t) == TTNS_OK &&
+         cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    if (!ok) last_err = g_err;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ttns_free(t);
+    if (ok && ms >= 0.0f && (best == 0 || ms * 1e-3 < best_s)) {
+      best = cand[k];
+      best_s = ms * 1e-3;
+    }
+  }
+  if (best == 0) return fail(TTNS_E_CUDA, "autotune: no candidate ran (" + last_err + ")");
+  *best_cluster_ctas = best;
+  if (best_seconds_per_step) *best_seconds_per_step = best_s;
+  return TTNS_OK;
+}
+
 extern "C" ttns_status ttns_build_tree(const ttns_problem* problem, const ttns_options* opt, ttns_tree** out) {
   return build(1, problem, opt, out);
 }

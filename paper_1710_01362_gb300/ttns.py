@@ -25,7 +25,7 @@ EXPORTS = [
     "ttns_occupations", "ttns_observables", "ttns_trajectory", "ttns_populations_device", "ttns_get_counters",
     "ttns_node_info", "ttns_get_node", "ttns_save", "ttns_load_state", "ttns_last_error", "ttns_free",
     "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan", "ttns_selftest_wait_timeout",
-    "ttns_rho_from_root_noalloc",
+    "ttns_rho_from_root_noalloc", "ttns_autotune",
 ]
 
 
@@ -84,6 +84,8 @@ def lib():
         L.ttns_build_tree.argtypes = [C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(C.c_void_p)]
         L.ttns_build_batch.argtypes = [C.c_int, C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(C.c_void_p)]
         L.ttns_step.argtypes = [C.c_void_p, C.c_double, C.c_int]
+        L.ttns_autotune.argtypes = [C.c_int, C.POINTER(ProblemC), C.POINTER(Options), C.c_double, C.c_int,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
         L.ttns_sync.argtypes = [C.c_void_p]
         L.ttns_reduced_density_matrix.argtypes = [C.c_void_p, C.c_int, dp]
         L.ttns_occupations.argtypes = [C.c_void_p, C.c_int, dp]
@@ -218,6 +220,25 @@ def plan(problems, precision: int = TTNS_MIXED, krylov_mmax: int = 0) -> dict:
             "apply_flops_per_step": info.apply_flops_per_step, "env_flops_per_step": info.env_flops_per_step,
             "exponentials_per_step": info.exponentials_per_step, "env_updates_per_step": info.env_updates_per_step,
             "bonds": [info.bonds[i] for i in range(info.n_bonds_written)]}
+
+
+def autotune(problems, dt: float, precision: int = TTNS_MIXED, candidates=None, stream: Optional[int] = None):
+    """Fastest number of CTAs per cluster team for this tree set (ttns_autotune); returns
+    (cluster_ctas, seconds_per_step)."""
+    probs = list(problems) if isinstance(problems, (list, tuple)) else [problems]
+    keep = [_ProblemKeep(p) for p in probs]
+    hold = []
+    if stream is None:
+        stream = current_stream()
+    opt = _options(probs[0], precision, stream=stream, keep=hold)
+    arr = (ProblemC * len(probs))(*[k.c for k in keep])
+    cand = list(candidates or [])
+    carr = (C.c_int * max(1, len(cand)))(*cand) if cand else None
+    best = C.c_int(0)
+    secs = C.c_double(0.0)
+    _check(lib().ttns_autotune(len(probs), arr, C.byref(opt), C.c_double(dt), len(cand), carr, C.byref(best),
+                               C.byref(secs)))
+    return best.value, secs.value
 
 
 class Tree:

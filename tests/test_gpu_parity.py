@@ -295,6 +295,24 @@ def test_plain_cluster_launch_equals_cooperative_launch():
     assert np.array_equal(r[0], r[1])
 
 
+def test_autotune_picks_a_cluster_size_that_matches_the_oracle():
+    # the autotuner times one step per candidate team shape on the real batch; a run with the
+    # chosen shape must still follow the oracle (cluster sizes 16, 8 and 4 all run here)
+    ps = [W.sf_small(seed=s, n_env=2, L=4, d=3, D=4, n_modes=8, n_steps=8) for s in (21, 22, 23, 24, 25, 26)]
+    best, secs = ttns.autotune(ps, ps[0].dt, precision=ttns.TTNS_FP64)
+    assert best in (16, 8, 4) and secs > 0
+    from oracle.ttns import TTNS
+    for c in (best, 4):
+        g = ttns.Tree(ps, precision=ttns.TTNS_FP64, cluster_ctas=c)
+        g.step(ps[0].dt, 8)
+        for k, p in enumerate(ps):
+            o = TTNS(p)
+            for _ in range(8):
+                o.step(p.dt)
+            assert np.abs(g.rho(k) - o.rho_el()).max() < 1e-7, (c, k)
+        g.close()
+
+
 def test_bounded_wait_reports_timeout():
     # a grid barrier that one CTA never reaches (a flag nothing sets): the waiting CTA gives
     # up after the bound, the status word reads TTNS_E_TIMEOUT and the context stays usable

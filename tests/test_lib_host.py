@@ -111,6 +111,11 @@ def test_invalid_arguments_are_rejected_before_any_allocation():
     assert e.value.code == 1
     with pytest.raises(ttns.TTNSError):
         ttns.chain_from_modes([0.1, 0.2], [0.01, 0.02], 3)
+    # the autotuner checks its arguments before it builds anything
+    for cand, dt in (([0], 0.5), ([17], 0.5), ([8], 0.0), ([8], float("nan"))):
+        with pytest.raises(ttns.TTNSError) as e:
+            ttns.autotune(p, dt, candidates=cand, stream=0)
+        assert e.value.code == 1
 
 
 def test_flop_accounting_of_the_root_apply():
