@@ -180,7 +180,7 @@ def main():
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    from paper_1710_01362_gb300 import build, ttns
+    from paper_1710_01362_gb300 import build, shard, ttns
     from paper_1710_01362_gb300 import workloads as W
     if rank == 0 or world > 1:
         build.build()
@@ -200,8 +200,7 @@ def main():
         tree.sync()
         c0 = tree.counters()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        if world > 1:
-            torch.distributed.barrier()
+        shard.barrier()
         torch.cuda.synchronize()
         clocks = ClockSampler(dev.index)
         clocks.start()
@@ -215,12 +214,9 @@ def main():
         tree.sync()
         times = [a.elapsed_time(b) for a, b in ev]  # ms
         c1 = tree.counters()
-        total_ms = float(sum(times))
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(t.item())
-        value = world * K / (total_ms * 1e-3)
+        shard.barrier()
+        total_ms = shard.max_over_ranks(float(sum(times)))  # the slowest replica's time
+        value = shard.aggregate_rate(K, world, total_ms * 1e-3)
 
         # populations vs the oracle's stored trajectory (steps 1..Wm+K)
         pop_err = None
@@ -250,8 +246,8 @@ def main():
             t2.step(p.dt, 1)
             ttns.lib().ttns_reduced_density_matrix(t2.h, 0, ttns._dptr(rho_np))
         t2.close()
-        e2e_s = time.perf_counter() - t0
-        e2e_value = world * K / e2e_s
+        e2e_s = shard.max_over_ranks(time.perf_counter() - t0)
+        e2e_value = shard.aggregate_rate(K, world, e2e_s)
 
     flops = c1["contraction_flops"] - c0["contraction_flops"]
     iters = c1["krylov_iters"] - c0["krylov_iters"]
