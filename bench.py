@@ -31,7 +31,7 @@ sys.path.insert(0, HERE)
 
 # DRAM bytes (read + write) of one k_sweep launch (one headline step), from one ncu capture
 # of dram__bytes_read.sum + dram__bytes_write.sum for this kernel build (mean of two launches)
-KSWEEP_DRAM_BYTES_PER_STEP = 664.03e6
+KSWEEP_DRAM_BYTES_PER_STEP = 664.14e6
 
 METRIC = "ttns_sweeps_per_s"
 UNIT = "sweeps/s"

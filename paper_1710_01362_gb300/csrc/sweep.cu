@@ -996,8 +996,8 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
       m = j + 1;
       const double est = bnext * lead;
       lead *= fabs(s_rem) * bnext / (double)m;
-      if ((est <= 1e3 * P.tol && m >= next_check) || m == mmax || !(bnext > 0.0)) {
-        next_check = m + 2;
+      if ((est <= 1e2 * P.tol && m >= next_check) || m == mmax || !(bnext > 0.0)) {
+        next_check = m + 1;
         if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s_rem, ks.ure, ks.uim);
         __syncthreads();
         const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);
@@ -1349,8 +1349,8 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
       m = j + 1;
       const double est = bnext * lead;
       lead *= fabs(s_rem) * bnext / (double)m;
-      if ((est <= 1e3 * P.tol && m >= next_check) || m == mmax || !(bnext > 0.0)) {
-        next_check = m + 2;
+      if ((est <= 1e2 * P.tol && m >= next_check) || m == mmax || !(bnext > 0.0)) {
+        next_check = m + 1;
         if (threadIdx.x < 32) texp_warp(ks.alpha, ks.beta, m, s_rem, ks.ure, ks.uim);
         __syncthreads();
         const double um = sqrt(ks.ure[m - 1] * ks.ure[m - 1] + ks.uim[m - 1] * ks.uim[m - 1]);

@@ -139,3 +139,40 @@ def test_truncated_bond_error_vs_exact_is_small_but_nonzero():
         psi = ex.state(st.t)
         err = max(err, np.abs(st.populations() - np.real(np.diag(ex.rho_el(psi)))).max())
     assert 1e-8 < err < 1e-2
+
+
+def test_density_matrix_is_hermitian_unit_trace_and_positive():
+    # reduced density matrix of an evolved truncated tree: a physical state
+    p = W.sf_small(seed=7, n_env=3, L=4, d=3, D=4, n_modes=8)
+    st = TTNS(p)
+    for _ in range(4):
+        st.step(p.dt)
+    rho = st.rho_el()
+    assert np.abs(rho - rho.conj().T).max() < 1e-14
+    assert abs(np.trace(rho).real - 1.0) < 1e-10
+    assert np.linalg.eigvalsh(0.5 * (rho + rho.conj().T)).min() > -1e-12
+    occ = st.occupations()
+    assert np.all(occ > -1e-12) and np.all(occ < p.envs[0].d)
+
+
+def test_observables_are_invariant_under_a_bond_gauge_change():
+    # a random unitary U on every bond (U on the parent's leg, conj(U) on the child's parent
+    # leg) leaves the state, rho_S and the site occupations unchanged and keeps the child an
+    # isometry toward its parent
+    from oracle.ttns import apply_factor
+    p = W.sf_small(seed=11, n_env=2, L=3, d=3, D=4, n_modes=6)
+    st = TTNS(p)
+    for _ in range(3):
+        st.step(p.dt)
+    psi0, rho0, occ0 = st.to_dense(), st.rho_el(), st.occupations()
+    rng = np.random.default_rng(5)
+    tr = st.tree
+    for v in range(tr.n):
+        for c in tr.children[v]:
+            D = st.A[c].shape[0]
+            U, _ = np.linalg.qr(rng.normal(size=(D, D)) + 1j * rng.normal(size=(D, D)))
+            st.A[v] = apply_factor(st.A[v], tr.leg_of(v, c), U)
+            st.A[c] = apply_factor(st.A[c], tr.leg_of(c, v), U.conj())
+    assert np.abs(st.to_dense() - psi0).max() < 1e-12
+    assert np.abs(st.rho_el() - rho0).max() < 1e-12
+    assert np.abs(st.occupations() - occ0).max() < 1e-12
