@@ -1,9 +1,10 @@
 """One-site TDVP for a tree tensor network state (oracle; test infrastructure only).
 
-The paper evolves its TTNS with the time-dependent variational principle: every
-tensor is evolved in turn with a local effective Hamiltonian H_eff(t) built from
-the full many-body state at that moment (Results, "TTNS for vibronic quantum
-dynamics", last paragraph; Methods, "Tensor Network States").  The algorithm
+The paper propagates its TTNS with the time-dependent variational principle: the
+tensors are updated one after another, each under a local effective Hamiltonian
+H_eff(t) that is rebuilt at every step from the current state of the whole tree
+(Results, section on TTNS for vibronic dynamics, last paragraph; Methods, section on
+tensor network states).  The algorithm
 itself sits in the paper's Supplement, which is not part of the paper text; the
 reading used here is the one-site projector-splitting integrator on a tree:
 
