@@ -238,7 +238,11 @@ ttns_status ttns_selftest_wait_timeout(long long spin_limit, int* device_status)
 ttns_status ttns_rho_from_root_noalloc(const double* d_root, long long rows, int n_el, double* d_rho,
                                        void* cuda_stream);
 
+/* Message of the last failing call made by the calling host thread (thread-local storage
+ * owned by the library; valid until that thread's next failing call). */
 const char* ttns_last_error(void);
+/* Waits for the tree set's stream, then releases every device buffer and the handle.
+ * NULL is accepted (no-op).  The handle must not be used afterwards. */
 void ttns_free(ttns_tree* tree);
 
 /* Chain maps (host, FP64).  ttns_chain_ohmic: closed form for the Ohmic density
