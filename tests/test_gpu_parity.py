@@ -313,6 +313,34 @@ def test_autotune_picks_a_cluster_size_that_matches_the_oracle():
         g.close()
 
 
+EDGE = {
+    # one-site chains, the minimal local dimension, bond dimension 1 (product states), a single
+    # electronic state, and an ER tree over two chains
+    "L1_chains": dict(seed=41, n_env=3, L=1, d=4, D=4, n_el=3),
+    "d2_local": dict(seed=42, n_env=2, L=4, d=2, D=3, n_el=4),
+    "D1_product": dict(seed=43, n_env=2, L=3, d=3, D=1, n_el=4),
+    "n_el_1": dict(seed=44, n_env=1, L=3, d=3, D=3, n_el=1),
+    "er_2_chains": dict(seed=45, n_env=2, L=2, d=3, D=3, n_el=4, er_tree=True, D_er=4),
+}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(EDGE))
+def test_edge_trees_match_oracle(name, prec):
+    from oracle.ttns import TTNS
+    kw = dict(EDGE[name])
+    p = W.singlet_fission(n_modes=6, dt=0.5, n_steps=6, name="edge_" + name, **kw)
+    g, pops = run_traj(p, p.n_steps, prec)
+    o = TTNS(p)
+    ref = []
+    for _ in range(p.n_steps):
+        o.step(p.dt)
+        ref.append(o.populations())
+    err = np.abs(pops - np.array(ref)).max()
+    assert err < TOL[prec], f"{name}: max population error {err:.3e}"
+    g.close()
+
+
 def test_bounded_wait_reports_timeout():
     # a grid barrier that one CTA never reaches (a flag nothing sets): the waiting CTA gives
     # up after the bound, the status word reads TTNS_E_TIMEOUT and the context stays usable
