@@ -44,15 +44,31 @@ typedef enum {
   TTNS_E_INVALID = 1,       /* bad argument */
   TTNS_E_OOM = 2,           /* device allocation failed */
   TTNS_E_CUDA = 3,          /* a CUDA call failed */
-  TTNS_E_NOT_CONVERGED = 4, /* a Krylov exponential hit krylov_mmax above tolerance */
+  TTNS_E_NOT_CONVERGED = 4, /* a Krylov exponential did not cover its time step within 64
+                               Krylov spaces of dimension krylov_mmax (each space takes the
+                               largest s / 2^k, k <= 30, that reaches krylov_tol) */
   TTNS_E_TIMEOUT = 5,       /* a device-side wait gave up (bounded spin) */
   TTNS_E_NONFINITE = 6,     /* a norm became NaN or Inf */
   TTNS_E_IO = 7             /* checkpoint file error */
 } ttns_status;
 
+/* Precision of the contractions (H_eff / H_bond applications and environment updates).  In
+ * every mode the Krylov basis and recurrence, the small exponential, the QR bond steps, the
+ * gauge absorbs and the observables are FP64.
+ *   TTNS_FP64    every contraction in FP64;
+ *   TTNS_TF32X3  split-precision tensor cores: the H_eff applications of tensors of at least 4096
+ *                elements whose terms have one dense factor each are complex GEMMs on tcgen05 with
+ *                3xTF32 operands (hi*hi + hi*lo + lo*hi) and FP32 accumulation in tensor memory;
+ *                every other contraction in FP32 on the SIMT cores;
+ *   TTNS_BF16X3  the same with a 3-way BF16 split and the 6 products of order <= 2^-16;
+ *   TTNS_FP32    every contraction in FP32 on the SIMT cores.
+ * TTNS_MIXED is TTNS_TF32X3. */
 typedef enum {
-  TTNS_FP64 = 0,  /* every contraction in FP64 */
-  TTNS_MIXED = 1  /* contractions in FP32-class arithmetic with FP64 Lanczos, QR, gauge moves */
+  TTNS_FP64 = 0,
+  TTNS_TF32X3 = 1,
+  TTNS_MIXED = 1,
+  TTNS_BF16X3 = 2,
+  TTNS_FP32 = 3
 } ttns_precision;
 
 typedef struct {
@@ -61,15 +77,16 @@ typedef struct {
   int krylov_mmax;       /* maximum Krylov dimension, 0 -> 30 (at most 32) */
   void* cuda_stream;     /* cudaStream_t used by every call, NULL = default stream */
   int er_tree;           /* 1: balanced binary ER tree between the root and the chains */
-  int D_er;              /* requested bond dimension between ER nodes (er_tree only) */
+  int D_er;              /* requested bond dimension between ER nodes (er_tree only; clamped like bond_dim) */
   int init_state;        /* electronic state populated at t = 0 (when psi_el is NULL) */
   const double* psi_el;  /* optional initial electronic amplitudes, n_el complex (copied) */
   int record;            /* 1: keep rho_S after every step in a device trajectory buffer */
   int max_record;        /* capacity of that buffer in steps (0 -> 4096) */
   int cluster_ctas;      /* CTAs per cluster team (0 -> 16) */
   int grid_ctas;         /* CTAs of the persistent grid (0 -> as many as can be co-resident) */
-  int grid_threshold;    /* single tree: tensors with at least this many elements are handled by the
-                            whole grid, smaller ones by one cluster (0 -> 65536) */
+  int grid_threshold;    /* single tree: Krylov exponentials, environment updates and absorbs of tensors
+                            with at least this many elements are handled by the whole grid, smaller
+                            ones by one cluster (0 -> 16384) */
   long long spin_limit;  /* bound of every device-side wait, in SM clock cycles (0 -> 2e10);
                             a wait that runs out sets TTNS_E_TIMEOUT */
   int profile;           /* 1: accumulate per-op device time (see ttns_counters) */
@@ -78,7 +95,16 @@ typedef struct {
                             of cooperative launches).  Co-residency of the grid then rests on the
                             grid fitting an otherwise idle GPU; a grid barrier that cannot complete
                             ends in TTNS_E_TIMEOUT.  A launch whose cluster shape or shared memory
-                            differs from the plan sets TTNS_E_CUDA before any work. */
+                            differs from the plan returns before any work; the next synchronising
+                            call repeats it (and every step launched since) once as a plain
+                            cluster launch, counted in ttns_counters.launch_fallbacks.
+                            bit 1: fault injection for tests: step launches get clusters of one
+                            CTA, which the kernel refuses, until that repeat has happened. */
+  int qr_grid_threshold; /* single tree: the same choice for the QR bond steps (0 -> 65536); QRs keep a
+                            column-serial reduction chain, so they favour the smaller team longer */
+  double qr_cutoff;      /* relative null threshold of the QR bond step (0 -> 1e-8): a sub-column whose
+                            norm is at most qr_cutoff * ||M||_F is completed by the identity reflector
+                            and its content is dropped (see the oracle's QR reading) */
 } ttns_options;
 
 /* One tree's Hamiltonian (Eq. 2) and truncation.
@@ -93,7 +119,9 @@ typedef struct {
  *   local_dim       n_env: Fock truncation d_i >= 2 of every site of chain i
  *   bond_dim        n_env: requested bond dimension D_i >= 1 along chain i (and to its parent)
  * Bond dimensions are clamped to the largest values with D_e <= product of the
- * other leg dimensions at both ends of every bond. */
+ * other leg dimensions at both ends of every bond, so any request at least as large as
+ * the Hilbert space (e.g. 1 << 20) asks for the full bond dimension.  A bond that still
+ * exceeds 64 after that clamp gives TTNS_E_INVALID. */
 typedef struct {
   int n_el;
   const double* H_S;
@@ -200,6 +228,9 @@ typedef struct {
   /* the same two breakdowns for the grid-team (whole-GPU) operations */
   double expm_phase_seconds_grid[8];
   double qr_phase_seconds_grid[8];
+  /* launches of the persistent kernel that its launch check refused (no planned cluster
+   * shape, e.g. under a profiler) and that were repeated as plain cluster launches */
+  long long launch_fallbacks;
 } ttns_counters;
 ttns_status ttns_get_counters(ttns_tree* tree, ttns_counters* out);
 
@@ -209,8 +240,17 @@ ttns_status ttns_get_counters(ttns_tree* tree, ttns_counters* out);
 ttns_status ttns_node_info(ttns_tree* tree, int tree_idx, int node, int* n_legs, int* dims, int* n_nodes);
 ttns_status ttns_get_node(ttns_tree* tree, int tree_idx, int node, double* out, size_t n_complex);
 
-/* Writes / reads a checkpoint: every tree's tensors, time and step count. */
+/* Checkpoints.  ttns_save writes every tree's problem (H_S, patterns, chains, dimensions,
+ * ER layout, initial amplitudes), the recording settings, and the whole device state
+ * (tensors, environment blocks, trajectory, time, step counters).
+ * ttns_load builds a new tree set from such a file alone and restores its state: the problem
+ * and the recording settings come from the file; the run options (precision, Krylov
+ * settings, stream, team shape) from *opt (NULL = defaults).  *out receives the new tree.
+ * ttns_load_state restores a file's state into an existing tree set of the same shape.
+ * Tensor contents are not validated on load: a non-finite entry is reported by the next
+ * step as TTNS_E_NONFINITE.  A missing, truncated or mismatching file gives TTNS_E_IO. */
 ttns_status ttns_save(ttns_tree* tree, const char* path);
+ttns_status ttns_load(const char* path, const ttns_options* opt, ttns_tree** out);
 ttns_status ttns_load_state(ttns_tree* tree, const char* path);
 
 /* Self-test of the device-side bounded wait (no counterpart in the paper: failure
@@ -219,6 +259,17 @@ ttns_status ttns_load_state(ttns_tree* tree, const char* path);
  * *device_status receives TTNS_E_TIMEOUT.  With spin_limit == 0 both arrive and
  * *device_status receives TTNS_OK.  Uses the legacy default stream. */
 ttns_status ttns_selftest_wait_timeout(long long spin_limit, int* device_status);
+
+/* Self-test of the tensor-core tile GEMM behind the split-precision contractions (no
+ * counterpart in the paper: a check of this library's building block).  Computes the complex
+ * product Y[m][n] = sum_k Z[m][k] Mt[n][k] on one CTA with tcgen05 MMAs, as a real GEMM of 2 x 2
+ * blocks with FP32 accumulation in tensor memory, in split precision kind = 1 (TF32X3: 3 TF32
+ * products) or kind = 2 (BF16X3: 6 BF16 products of a 3-way split).  Z: M x K, Mt: N x K,
+ * Y: M x N complex (interleaved doubles, row-major, host buffers); 1 <= M <= 4096,
+ * 1 <= K <= 1024, 1 <= N <= 64.  *device_status receives TTNS_E_TIMEOUT if a completion
+ * wait gave up, else TTNS_OK.  Allocates device memory; synchronises the device. */
+ttns_status ttns_selftest_tc_gemm(int kind, int M, int K, int N, const double* Z, const double* Mt, double* Y,
+                                  int* device_status);
 
 /* Electronic reduced density matrix from a root tensor in caller-owned device
  * memory, allocating nothing (the paper has no counterpart: this is for callers
@@ -233,7 +284,8 @@ ttns_status ttns_selftest_wait_timeout(long long spin_limit, int* device_status)
  * Partial sums go to a fixed 1 MiB scratch array owned by the library on every
  * device that loads it; n_el > 16 is rejected with TTNS_E_INVALID.  The first call
  * on a device looks up that array's address (with the device current): make it
- * before any stream capture.  Calls share the array, so calls that overlap on the
+ * before any stream capture, and do not use the call across a cudaDeviceReset (the
+ * remembered address belongs to the context that was reset).  Calls share the array, so calls that overlap on the
  * GPU race; each call overwrites all the partials it uses.  Asynchronous. */
 ttns_status ttns_rho_from_root_noalloc(const double* d_root, long long rows, int n_el, double* d_rho,
                                        void* cuda_stream);

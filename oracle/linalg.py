@@ -63,7 +63,9 @@ def householder_qr(M: np.ndarray):
             W[j + 1:, j] = 0.0
             continue
         x0 = x[0]
-        phase = x0 / abs(x0) if abs(x0) > 0.0 else 1.0 + 0.0j
+        # a head below 1e-280 (far below any amplitude that matters; its reciprocal would
+        # overflow) is treated as zero: phase 1
+        phase = x0 / abs(x0) if abs(x0) > 1e-280 else 1.0 + 0.0j
         alpha = -phase * sigma
         v = x.copy()
         v[0] -= alpha

@@ -39,6 +39,7 @@ static ttns_status fail(ttns_status st, const std::string& msg) {
 
 struct ttns_tree {
   Compiled C;
+  std::vector<TreeInput> inputs;  // validated problems (written into checkpoints)
   ttns_options opt{};
   bool batched = false;
   int grid = 0, cluster = 16;
@@ -65,7 +66,21 @@ struct ttns_tree {
   KernelParams P{};
   std::vector<void*> allocs;
   double t_fs = 0.0;
+  // step launches not yet confirmed by a synchronising call (dt, n), and how often a launch
+  // was repeated as a plain cluster launch (see run_launch)
+  std::vector<std::pair<double, int>> pending;
+  long long launch_fallbacks = 0;
 };
+
+// Launch of the persistent kernel with the tree set's launch options.  launch_flags bit 1 is a
+// host-side fault injection for tests: step launches get clusters of one CTA (as a profiler
+// that drops the cluster shape of cooperative launches would give them) until the library has
+// switched to plain cluster launches; the kernel's launch check refuses each before any
+// barrier or distributed-shared-memory access.
+static cudaError_t launch_persistent(ttns_tree* t, const ttns::KernelParams& P, int phase) {
+  const bool inject = (t->opt.launch_flags & 2) && !(t->opt.launch_flags & 1) && phase == 1;
+  return ttns::launch_sweep(P, phase, t->grid, inject ? 1 : t->cluster, !(t->opt.launch_flags & 1), t->stream);
+}
 
 static const char* kStatusNames[] = {"ok", "invalid", "oom", "cuda", "not converged", "timeout", "nonfinite", "io"};
 
@@ -128,7 +143,7 @@ static ttns_status validate(const ttns_problem* p, const ttns_options* opt, Tree
   const int er = opt ? opt->er_tree : 0;
   if (er && (p->n_env < 2 || (p->n_env & (p->n_env - 1)) != 0))
     return fail(TTNS_E_INVALID, "er_tree needs a power-of-two number of environments >= 2");
-  if (er && (opt->D_er < 1 || opt->D_er > TTNS_MAX_D)) return fail(TTNS_E_INVALID, "D_er out of range");
+  if (er && opt->D_er < 1) return fail(TTNS_E_INVALID, "D_er must be >= 1");
   const int ne = p->n_el;
   if (!hermitian(p->H_S, ne)) return fail(TTNS_E_INVALID, "H_S is not Hermitian");
   in->n_el = ne;
@@ -156,7 +171,7 @@ static ttns_status validate(const ttns_problem* p, const ttns_options* opt, Tree
       in->hop.emplace_back();
     in->L.push_back(L);
     in->d.push_back(d);
-    in->D.push_back(std::min(D, TTNS_MAX_D));
+    in->D.push_back(D);
   }
   in->er_tree = er;
   in->D_er = er ? opt->D_er : 0;
@@ -268,7 +283,9 @@ static ttns_status plan_sizes(const Compiled& C, const ttns_options& o, Sizes* z
   if (1 + z->maxchan > z->mmax) return fail(TTNS_E_INVALID, "too many coupling channels for krylov_mmax");
   if (C.max_D > TTNS_MAX_D) return fail(TTNS_E_INVALID, "a bond dimension exceeds 64");
   z->kvec = ((long long)C.max_node + 31) / 32 * 32;
-  z->work_stride = (long long)(z->mmax + std::max(C.max_tmp, 1) + 2) * z->kvec;
+  // Krylov vectors, two-factor temporaries, the compute-type shadow and a spare slot, and four
+  // slots for the tensor-core group results (up to eight compute-type vectors)
+  z->work_stride = (long long)(z->mmax + std::max(C.max_tmp, 1) + 2 + 4) * z->kvec;
   long long per_cta = 8;
   per_cta = std::max<long long>(per_cta, 2LL * C.max_D * C.max_D);
   per_cta = std::max<long long>(per_cta, 2LL * (1 + z->maxchan) * C.max_D * C.max_D);
@@ -276,6 +293,46 @@ static ttns_status plan_sizes(const Compiled& C, const ttns_options& o, Sizes* z
   per_cta = std::max<long long>(per_cta, 2LL * (TTNS_KMAX + 1));  // reorthogonalisation dots
   z->per_cta = per_cta;
   return check_tables(C, z->mmax, z->kvec, per_cta, std::max(C.max_tmp, 1));
+}
+
+// A persistent launch refused by the kernel's own launch check: it returned before any work
+// because it did not get the planned cluster shape (a profiler re-launches a cooperative
+// cluster launch with clusters of one CTA).
+static bool launch_refused(const Ctl& h) { return h.status == TTNS_E_CUDA && h.err_where == 300; }
+
+// Waits for the tree's stream and reads the device status word.  Launches that the kernel's
+// launch check refused are repeated once, in order, as plain cluster launches (launch_flags
+// bit 0), which keep their cluster shape under such tools: the initial environment pass when
+// `phase0`, then every step launched since the last check.  Nothing ran in the refused
+// launches, so the repeat is the computation that was asked for.
+static ttns_status wait_and_check(ttns_tree* t, bool phase0, const char* what) {
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  Ctl h;
+  CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  if (launch_refused(h) && !(t->opt.launch_flags & 1)) {
+    t->opt.launch_flags |= 1;
+    ++t->launch_fallbacks;
+    h.status = 0;
+    h.err_where = 0;
+    h.err_node = 0;
+    CUDA_TRY(cudaMemcpy(t->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
+    if (phase0) {
+      KernelParams P0 = t->P;
+      P0.dt = 0.0;
+      P0.n_steps = 1;
+      CUDA_TRY(launch_sweep(P0, 0, t->grid, t->cluster, 0, t->stream));
+    }
+    for (const auto& pr : t->pending) {
+      t->P.dt = pr.first;
+      t->P.n_steps = pr.second;
+      CUDA_TRY(launch_sweep(t->P, 1, t->grid, t->cluster, 0, t->stream));
+    }
+    CUDA_TRY(cudaStreamSynchronize(t->stream));
+    CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  }
+  t->pending.clear();
+  if (h.status != 0) return fail((ttns_status)h.status, std::string(what) + status_text(h));
+  return TTNS_OK;
 }
 
 static ttns_status device_init(ttns_tree* t) {
@@ -372,40 +429,53 @@ static ttns_status device_init(ttns_tree* t) {
   P.profile = o.profile;
   P.smem_bytes = smem_bytes;
   P.cluster_resident = 1;
+  P.qr_cutoff = o.qr_cutoff > 0.0 ? o.qr_cutoff : 1e-8;
   // initial environment pass
-  CUDA_TRY(launch_sweep(P, 0, t->grid, t->cluster, !(t->opt.launch_flags & 1), t->stream));
-  CUDA_TRY(cudaStreamSynchronize(t->stream));
-  Ctl h;
-  CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-  if (h.status != 0)
-    return fail((ttns_status)h.status, std::string("device status after the initial pass: ") + status_text(h));
+  CUDA_TRY(launch_persistent(t, P, 0));
+  return wait_and_check(t, true, "device status after the initial pass: ");
+}
+
+static ttns_status check_options(const ttns_options& o) {
+  if (o.precision < TTNS_FP64 || o.precision > TTNS_FP32) return fail(TTNS_E_INVALID, "unknown precision");
+  if (o.krylov_mmax < 0 || o.krylov_mmax > TTNS_KMAX) return fail(TTNS_E_INVALID, "krylov_mmax out of range (0..32)");
+  if (o.krylov_tol < 0) return fail(TTNS_E_INVALID, "krylov_tol < 0");
+  if (o.max_record < 0) return fail(TTNS_E_INVALID, "max_record < 0");
+  if (o.grid_threshold < 0 || o.qr_grid_threshold < 0 || o.spin_limit < 0)
+    return fail(TTNS_E_INVALID, "negative grid_threshold, qr_grid_threshold or spin_limit");
+  if (!(o.qr_cutoff >= 0.0 && o.qr_cutoff < 1.0)) return fail(TTNS_E_INVALID, "qr_cutoff must be in [0, 1)");
+  return TTNS_OK;
+}
+
+// Builds the host model and the compiled step of validated inputs into t.
+static ttns_status compile_inputs(std::vector<TreeInput> ins, const ttns_options& o, ttns_tree* t) {
+  ttns_status s = check_options(o);
+  if (s != TTNS_OK) return s;
+  t->opt = o;
+  t->opt.psi_el = nullptr;
+  t->batched = ins.size() > 1;
+  t->stream = (cudaStream_t)o.cuda_stream;
+  try {
+    t->C = compile_trees(ins, t->batched, o.grid_threshold > 0 ? o.grid_threshold : 16384,
+                         o.qr_grid_threshold > 0 ? o.qr_grid_threshold : 65536, o.max_record > 0 ? o.max_record : 4096,
+                         o.record);
+  } catch (const std::exception& e) {
+    return fail(TTNS_E_INVALID, std::string("model: ") + e.what());
+  }
+  t->inputs = std::move(ins);
   return TTNS_OK;
 }
 
 static ttns_status compile_only(int n_trees, const ttns_problem* probs, const ttns_options* opt, ttns_tree* t) {
   ttns_options o{};
   if (opt) o = *opt;
-  if (o.precision != TTNS_FP64 && o.precision != TTNS_MIXED) return fail(TTNS_E_INVALID, "unknown precision");
-  if (o.krylov_mmax < 0 || o.krylov_mmax > TTNS_KMAX) return fail(TTNS_E_INVALID, "krylov_mmax out of range (0..32)");
-  if (o.krylov_tol < 0) return fail(TTNS_E_INVALID, "krylov_tol < 0");
-  if (o.max_record < 0) return fail(TTNS_E_INVALID, "max_record < 0");
-  if (o.grid_threshold < 0 || o.spin_limit < 0) return fail(TTNS_E_INVALID, "negative grid_threshold or spin_limit");
+  ttns_status s = check_options(o);
+  if (s != TTNS_OK) return s;
   std::vector<TreeInput> ins(n_trees);
   for (int i = 0; i < n_trees; ++i) {
-    ttns_status s = validate(&probs[i], &o, &ins[i]);
+    s = validate(&probs[i], &o, &ins[i]);
     if (s != TTNS_OK) return s;
   }
-  t->opt = o;
-  t->opt.psi_el = nullptr;
-  t->batched = n_trees > 1;
-  t->stream = (cudaStream_t)o.cuda_stream;
-  try {
-    t->C = compile_trees(ins, t->batched, o.grid_threshold > 0 ? o.grid_threshold : 65536,
-                         o.max_record > 0 ? o.max_record : 4096, o.record);
-  } catch (const std::exception& e) {
-    return fail(TTNS_E_INVALID, std::string("model: ") + e.what());
-  }
-  return TTNS_OK;
+  return compile_inputs(std::move(ins), o, t);
 }
 
 extern "C" ttns_status ttns_plan(int n_trees, const ttns_problem* problems, const ttns_options* opt,
@@ -443,18 +513,7 @@ extern "C" ttns_status ttns_plan(int n_trees, const ttns_problem* problems, cons
   return TTNS_OK;
 }
 
-static ttns_status build(int n_trees, const ttns_problem* probs, const ttns_options* opt, ttns_tree** out) {
-  if (!out) return fail(TTNS_E_INVALID, "out is NULL");
-  *out = nullptr;
-  if (n_trees < 1 || !probs) return fail(TTNS_E_INVALID, "no problems");
-  ttns_tree* t = new ttns_tree();
-  {
-    ttns_status s0 = compile_only(n_trees, probs, opt, t);
-    if (s0 != TTNS_OK) {
-      delete t;
-      return s0;
-    }
-  }
+static ttns_status finish_build(ttns_tree* t, ttns_tree** out) {
   ttns_status s = device_init(t);
   if (s != TTNS_OK) {
     std::string keep = g_err;
@@ -464,6 +523,29 @@ static ttns_status build(int n_trees, const ttns_problem* probs, const ttns_opti
   }
   *out = t;
   return TTNS_OK;
+}
+
+static ttns_status build(int n_trees, const ttns_problem* probs, const ttns_options* opt, ttns_tree** out) {
+  if (!out) return fail(TTNS_E_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n_trees < 1 || !probs) return fail(TTNS_E_INVALID, "no problems");
+  ttns_tree* t = new ttns_tree();
+  ttns_status s0 = compile_only(n_trees, probs, opt, t);
+  if (s0 != TTNS_OK) {
+    delete t;
+    return s0;
+  }
+  return finish_build(t, out);
+}
+
+static ttns_status build_inputs(std::vector<TreeInput> ins, const ttns_options& o, ttns_tree** out) {
+  ttns_tree* t = new ttns_tree();
+  ttns_status s0 = compile_inputs(std::move(ins), o, t);
+  if (s0 != TTNS_OK) {
+    delete t;
+    return s0;
+  }
+  return finish_build(t, out);
 }
 
 // Autotuner of the team shape: for each candidate number of CTAs per cluster team, build the
@@ -534,19 +616,15 @@ extern "C" ttns_status ttns_step(ttns_tree* t, double dt_fs, int n_steps) {
   if (n_steps == 0) return TTNS_OK;
   t->P.dt = dt_fs;
   t->P.n_steps = n_steps;
-  CUDA_TRY(launch_sweep(t->P, 1, t->grid, t->cluster, !(t->opt.launch_flags & 1), t->stream));
+  CUDA_TRY(launch_persistent(t, t->P, 1));
+  t->pending.emplace_back(dt_fs, n_steps);
   t->t_fs += dt_fs * n_steps;
   return TTNS_OK;
 }
 
 extern "C" ttns_status ttns_sync(ttns_tree* t) {
   if (!t) return fail(TTNS_E_INVALID, "tree is NULL");
-  CUDA_TRY(cudaStreamSynchronize(t->stream));
-  Ctl h;
-  CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
-  if (h.status != 0)
-    return fail((ttns_status)h.status, std::string("device status: ") + status_text(h));
-  return TTNS_OK;
+  return wait_and_check(t, false, "device status: ");
 }
 
 static int find_root_fwd_terms(ttns_tree* t, int tree_idx, int* n2) {
@@ -705,6 +783,7 @@ extern "C" ttns_status ttns_get_counters(ttns_tree* t, ttns_counters* out) {
   for (int k = 0; k < 8; ++k) out->qr_phase_seconds[k] = h.phase_cycles[8 + k] / hz;
   for (int k = 0; k < 8; ++k) out->expm_phase_seconds_grid[k] = h.phase_cycles_grid[k] / hz;
   for (int k = 0; k < 8; ++k) out->qr_phase_seconds_grid[k] = h.phase_cycles_grid[8 + k] / hz;
+  out->launch_fallbacks = t->launch_fallbacks;
   return TTNS_OK;
 }
 
@@ -735,7 +814,147 @@ extern "C" ttns_status ttns_get_node(ttns_tree* t, int tree_idx, int node, doubl
   return TTNS_OK;
 }
 
-static const char kMagic[8] = {'T', 'T', 'N', 'S', 'C', 'K', 'P', '1'};
+// Checkpoint format (little-endian host types):
+//   "TTNSCKP2", int64 n_trees, every tree's problem (TreeInput: n_el, shifted-free H_S,
+//   patterns, chains, dims, requested bonds, ER layout, initial amplitudes), int32 record and
+//   max_record, then int64 {pool size, history slots, trees, 0}, double t_fs, the complex pool
+//   (tensors, environment blocks, trajectory), the Krylov-length history, the trajectory
+//   counters and the device control block.
+static const char kMagic[8] = {'T', 'T', 'N', 'S', 'C', 'K', 'P', '2'};
+
+namespace {
+struct Writer {
+  FILE* f;
+  bool ok = true;
+  template <typename T> void put(const T& x) { ok = ok && std::fwrite(&x, sizeof(T), 1, f) == 1; }
+  template <typename T> void put_vec(const std::vector<T>& v) {
+    put((long long)v.size());
+    if (!v.empty()) ok = ok && std::fwrite(v.data(), sizeof(T), v.size(), f) == v.size();
+  }
+};
+struct Reader {
+  FILE* f;
+  bool ok = true;
+  template <typename T> void get(T& x) { ok = ok && std::fread(&x, sizeof(T), 1, f) == 1; }
+  template <typename T> void get_vec(std::vector<T>& v, long long max_n) {
+    long long n = -1;
+    get(n);
+    if (!ok || n < 0 || n > max_n) { ok = false; return; }
+    v.resize(n);
+    if (n > 0) ok = ok && std::fread(v.data(), sizeof(T), n, f) == (size_t)n;
+  }
+};
+const long long kMaxVec = 1LL << 26;
+
+void write_input(Writer& w, const TreeInput& in) {
+  w.put(in.n_el);
+  w.put_vec(in.H_S);
+  w.put(in.n_env);
+  w.put((long long)in.W.size());
+  for (const auto& x : in.W) w.put_vec(x);
+  w.put_vec(in.rc);
+  w.put((long long)in.omega.size());
+  for (const auto& x : in.omega) w.put_vec(x);
+  w.put((long long)in.hop.size());
+  for (const auto& x : in.hop) w.put_vec(x);
+  w.put_vec(in.L);
+  w.put_vec(in.d);
+  w.put_vec(in.D);
+  w.put(in.er_tree);
+  w.put(in.D_er);
+  w.put_vec(in.psi_el);
+}
+
+bool read_input(Reader& r, TreeInput& in) {
+  long long n = 0;
+  r.get(in.n_el);
+  r.get_vec(in.H_S, kMaxVec);
+  r.get(in.n_env);
+  r.get(n);
+  if (!r.ok || n < 0 || n > 4096) return false;
+  in.W.resize(n);
+  for (auto& x : in.W) r.get_vec(x, kMaxVec);
+  r.get_vec(in.rc, kMaxVec);
+  r.get(n);
+  if (!r.ok || n < 0 || n > 4096) return false;
+  in.omega.resize(n);
+  for (auto& x : in.omega) r.get_vec(x, kMaxVec);
+  r.get(n);
+  if (!r.ok || n < 0 || n > 4096) return false;
+  in.hop.resize(n);
+  for (auto& x : in.hop) r.get_vec(x, kMaxVec);
+  r.get_vec(in.L, kMaxVec);
+  r.get_vec(in.d, kMaxVec);
+  r.get_vec(in.D, kMaxVec);
+  r.get(in.er_tree);
+  r.get(in.D_er);
+  r.get_vec(in.psi_el, kMaxVec);
+  if (!r.ok) return false;
+  // the shapes must agree with each other (the values were validated when the file was written)
+  const size_t ne = (size_t)in.n_env;
+  if (in.n_el < 1 || in.n_el > TTNS_MAX_D || in.n_env < 1 || in.H_S.size() != (size_t)in.n_el * in.n_el ||
+      in.W.size() != ne || in.rc.size() != ne || in.omega.size() != ne || in.hop.size() != ne || in.L.size() != ne ||
+      in.d.size() != ne || in.D.size() != ne || in.psi_el.size() != (size_t)in.n_el)
+    return false;
+  for (size_t i = 0; i < ne; ++i) {
+    if (in.W[i].size() != (size_t)in.n_el * in.n_el || in.L[i] < 1 || in.L[i] > 4096 ||
+        in.omega[i].size() != (size_t)in.L[i] || in.hop[i].size() != (size_t)std::max(in.L[i] - 1, 0) ||
+        in.d[i] < 2 || in.d[i] > TTNS_MAX_D || in.D[i] < 1)
+      return false;
+  }
+  return true;
+}
+
+// Reads the problem section of a checkpoint; leaves the file at the state section.
+ttns_status read_header(FILE* f, std::vector<TreeInput>* ins, int* record, int* max_record) {
+  char magic[8];
+  Reader r{f};
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0)
+    return fail(TTNS_E_IO, "not a TTNS checkpoint (bad magic)");
+  long long nt = 0;
+  r.get(nt);
+  if (!r.ok || nt < 1 || nt > (1 << 20)) return fail(TTNS_E_IO, "checkpoint: bad tree count");
+  ins->resize(nt);
+  for (auto& in : *ins)
+    if (!read_input(r, in)) return fail(TTNS_E_IO, "checkpoint: truncated or malformed problem section");
+  r.get(*record);
+  r.get(*max_record);
+  if (!r.ok) return fail(TTNS_E_IO, "checkpoint truncated");
+  return TTNS_OK;
+}
+
+// Reads the state section into an existing tree set of the same shape.
+ttns_status read_state(ttns_tree* t, FILE* f) {
+  long long hdr[4];
+  double tf = 0;
+  Reader r{f};
+  r.get(hdr);
+  r.get(tf);
+  if (!r.ok || hdr[0] != t->C.pool_size || hdr[1] != (long long)std::max(t->C.n_hist, 1) ||
+      hdr[2] != (long long)t->C.trees.size())
+    return fail(TTNS_E_IO, "checkpoint does not match this tree (or is truncated)");
+  std::vector<double2> pool(hdr[0]);
+  std::vector<int> mh(hdr[1]), tc(hdr[2]);
+  Ctl h;
+  bool ok = std::fread(pool.data(), sizeof(double2), pool.size(), f) == pool.size() &&
+            std::fread(mh.data(), sizeof(int), mh.size(), f) == mh.size() &&
+            std::fread(tc.data(), sizeof(int), tc.size(), f) == tc.size() && std::fread(&h, sizeof(Ctl), 1, f) == 1;
+  if (!ok) return fail(TTNS_E_IO, "checkpoint truncated");
+  // the tensors are not validated here: a non-finite entry is reported by the next step
+  // (TTNS_E_NONFINITE from the Krylov norm)
+  h.bar_count = 0;
+  h.bar_gen = 0;
+  h.status = 0;
+  h.err_where = 0;
+  h.err_node = 0;
+  CUDA_TRY(cudaMemcpy(t->pool, pool.data(), pool.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->mhist, mh.data(), mh.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->traj_count, tc.data(), tc.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CUDA_TRY(cudaMemcpy(t->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
+  t->t_fs = tf;
+  return TTNS_OK;
+}
+}  // namespace
 
 extern "C" ttns_status ttns_save(ttns_tree* t, const char* path) {
   if (!t || !path) return fail(TTNS_E_INVALID, "NULL argument");
@@ -750,10 +969,16 @@ extern "C" ttns_status ttns_save(ttns_tree* t, const char* path) {
   CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(TTNS_E_IO, std::string("cannot open ") + path);
+  Writer w{f};
+  w.ok = std::fwrite(kMagic, 1, 8, f) == 8;
+  w.put((long long)t->inputs.size());
+  for (const TreeInput& in : t->inputs) write_input(w, in);
+  w.put((int)t->opt.record);
+  w.put((int)t->P.max_record);
   long long hdr[4] = {(long long)pool.size(), (long long)mh.size(), (long long)tc.size(), 0};
-  bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(hdr), 1, f) == 1 &&
-            std::fwrite(&t->t_fs, sizeof(double), 1, f) == 1 &&
-            std::fwrite(pool.data(), sizeof(double2), pool.size(), f) == pool.size() &&
+  w.put(hdr);
+  w.put(t->t_fs);
+  bool ok = w.ok && std::fwrite(pool.data(), sizeof(double2), pool.size(), f) == pool.size() &&
             std::fwrite(mh.data(), sizeof(int), mh.size(), f) == mh.size() &&
             std::fwrite(tc.data(), sizeof(int), tc.size(), f) == tc.size() && std::fwrite(&h, sizeof(Ctl), 1, f) == 1;
   ok = (std::fclose(f) == 0) && ok;
@@ -767,32 +992,47 @@ extern "C" ttns_status ttns_load_state(ttns_tree* t, const char* path) {
   if (s != TTNS_OK) return s;
   FILE* f = std::fopen(path, "rb");
   if (!f) return fail(TTNS_E_IO, std::string("cannot open ") + path);
-  char magic[8];
-  long long hdr[4];
-  double tf = 0;
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
-            std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(&tf, sizeof(double), 1, f) == 1;
-  if (!ok || hdr[0] != t->C.pool_size || hdr[1] != (long long)std::max(t->C.n_hist, 1) ||
-      hdr[2] != (long long)t->C.trees.size()) {
-    std::fclose(f);
-    return fail(TTNS_E_IO, "checkpoint does not match this tree (or is truncated)");
-  }
-  std::vector<double2> pool(hdr[0]);
-  std::vector<int> mh(hdr[1]), tc(hdr[2]);
-  Ctl h;
-  ok = std::fread(pool.data(), sizeof(double2), pool.size(), f) == pool.size() &&
-       std::fread(mh.data(), sizeof(int), mh.size(), f) == mh.size() &&
-       std::fread(tc.data(), sizeof(int), tc.size(), f) == tc.size() && std::fread(&h, sizeof(Ctl), 1, f) == 1;
+  std::vector<TreeInput> ins;
+  int record = 0, max_record = 0;
+  s = read_header(f, &ins, &record, &max_record);
+  if (s == TTNS_OK) s = read_state(t, f);
   std::fclose(f);
-  if (!ok) return fail(TTNS_E_IO, "checkpoint truncated");
-  h.bar_count = 0;
-  h.bar_gen = 0;
-  h.status = 0;
-  CUDA_TRY(cudaMemcpy(t->pool, pool.data(), pool.size() * sizeof(double2), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(t->mhist, mh.data(), mh.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(t->traj_count, tc.data(), tc.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CUDA_TRY(cudaMemcpy(t->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
-  t->t_fs = tf;
+  return s;
+}
+
+static ttns_status build_inputs(std::vector<TreeInput> ins, const ttns_options& o, ttns_tree** out);
+
+extern "C" ttns_status ttns_load(const char* path, const ttns_options* opt, ttns_tree** out) {
+  if (!path || !out) return fail(TTNS_E_INVALID, "NULL argument");
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(TTNS_E_IO, std::string("cannot open ") + path);
+  std::vector<TreeInput> ins;
+  int record = 0, max_record = 0;
+  ttns_status s = read_header(f, &ins, &record, &max_record);
+  if (s != TTNS_OK) {
+    std::fclose(f);
+    return s;
+  }
+  ttns_options o{};
+  if (opt) o = *opt;
+  // the tree layout and the trajectory buffer come from the file (the pool must match)
+  o.er_tree = ins[0].er_tree;
+  o.D_er = ins[0].D_er;
+  o.psi_el = nullptr;
+  o.record = record;
+  o.max_record = max_record;
+  ttns_tree* t = nullptr;
+  s = build_inputs(std::move(ins), o, &t);
+  if (s == TTNS_OK) s = read_state(t, f);
+  std::fclose(f);
+  if (s != TTNS_OK) {
+    std::string keep = g_err;
+    ttns_free(t);
+    g_err = keep;
+    return s;
+  }
+  *out = t;
   return TTNS_OK;
 }
 

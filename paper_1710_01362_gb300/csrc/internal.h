@@ -160,6 +160,7 @@ struct KernelParams {
   int profile;
   long long smem_bytes;    // dynamic shared memory per CTA (operator matrices of one op)
   int cluster_resident;    // 1: small-node Krylov exponentials kept in the cluster's shared memory
+  double qr_cutoff;        // relative null threshold of the QR
 };
 
 }  // namespace ttns

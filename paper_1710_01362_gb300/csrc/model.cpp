@@ -25,6 +25,7 @@
 #include <functional>
 #include <map>
 #include <stdexcept>
+#include <string>
 
 namespace ttns {
 
@@ -178,9 +179,16 @@ HostTree build_host_tree(const TreeInput& in) {
     }
     t.chain_nodes.push_back(nodes);
   }
+  // requested bond dimensions (any size: a request beyond the Hilbert space asks for the full
+  // bond) are clamped first; what remains must fit the device code's leg limit
   clamp_bonds(t, req);
   t.bond.assign(t.n(), 0);
-  for (int v = 1; v < t.n(); ++v) t.bond[v] = (int)req[v];
+  for (int v = 1; v < t.n(); ++v) {
+    if (req[v] > TTNS_MAX_D)
+      throw std::invalid_argument("bond dimension " + std::to_string(req[v]) + " of node " + std::to_string(v) +
+                                  " exceeds " + std::to_string(TTNS_MAX_D) + " after the Hilbert-space clamp");
+    t.bond[v] = (int)req[v];
+  }
 
   // on-site operators
   t.onsite.assign(t.n(), {});
@@ -248,9 +256,10 @@ struct TreeCompiler {
   std::map<std::pair<int, int>, int> hist_slot;
   bool batched;
   int grid_threshold;
+  int qr_grid_threshold;
 
-  TreeCompiler(const HostTree& t_, Compiled& C_, int idx, bool b, int gt)
-      : t(t_), C(C_), tree_idx(idx), batched(b), grid_threshold(gt) {}
+  TreeCompiler(const HostTree& t_, Compiled& C_, int idx, bool b, int gt, int qgt)
+      : t(t_), C(C_), tree_idx(idx), batched(b), grid_threshold(gt), qr_grid_threshold(qgt) {}
 
   long long push_matrix(const std::vector<cplx>& m) {
     long long off = (long long)C.pool_init.size();
@@ -401,9 +410,9 @@ struct TreeCompiler {
     return d;
   }
 
-  int team_for(int size) const {
+  int team_for(int size, bool qr = false) const {
     if (batched) return TEAM_CLUSTER;
-    return size >= grid_threshold ? TEAM_GRID : TEAM_CLUSTER;
+    return size >= (qr ? qr_grid_threshold : grid_threshold) ? TEAM_GRID : TEAM_CLUSTER;
   }
 
   void compile() {
@@ -550,7 +559,7 @@ struct TreeCompiler {
     I.op = OP_QR;
     I.tree = tree_idx;
     I.node = node0 + v;
-    I.team = team_for(C.nodes[I.node].size);
+    I.team = team_for(C.nodes[I.node].size, true);
     I.leg = t.leg_of(v, u);
     I.D = C.nodes[I.node].dims[I.leg];
     C.prog.push_back(I);
@@ -676,14 +685,14 @@ struct TreeCompiler {
 
 }  // namespace
 
-Compiled compile_trees(const std::vector<TreeInput>& inputs, bool batched, int grid_threshold, int max_record,
-                       int record) {
+Compiled compile_trees(const std::vector<TreeInput>& inputs, bool batched, int grid_threshold,
+                       int qr_grid_threshold, int max_record, int record) {
   Compiled C;
   for (size_t i = 0; i < inputs.size(); ++i) {
     C.host.push_back(build_host_tree(inputs[i]));
   }
   for (size_t i = 0; i < inputs.size(); ++i) {
-    TreeCompiler tc(C.host[i], C, (int)i, batched, grid_threshold);
+    TreeCompiler tc(C.host[i], C, (int)i, batched, grid_threshold, qr_grid_threshold);
     tc.compile();
   }
   // trajectory buffers at the end of the pool

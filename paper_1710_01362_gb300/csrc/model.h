@@ -75,8 +75,10 @@ struct Compiled {
   std::vector<double> flops_per_instr;       // useful flops of one apply of each instruction's operator
 };
 
-// grid_threshold: tensors at least this large use the whole-grid team (single-tree mode).
-Compiled compile_trees(const std::vector<TreeInput>& inputs, bool batched, int grid_threshold, int max_record,
+// grid_threshold: tensors at least this large use the whole-grid team (single-tree mode) for
+// Krylov exponentials, environment updates and absorbs; qr_grid_threshold the same for QRs.
+Compiled compile_trees(const std::vector<TreeInput>& inputs, bool batched, int grid_threshold,
+                       int qr_grid_threshold, int max_record,
                        int record);
 
 void chain_ohmic(double alpha, double omega_c, int L, double* rc, double* onsite, double* hop);

@@ -14,6 +14,11 @@
 // device (cudaGetSymbolAddress, with that device current) on the first call made
 // on that device; make that first call before any stream capture.
 //
+// The looked-up address belongs to the device's current context: after a
+// cudaDeviceReset (or any reset of the primary context) the module is loaded again
+// and the remembered address is stale, so the entry point must not be used across
+// such a reset within one process.
+//
 // All calls share the one array, so two calls whose kernels overlap on the GPU
 // race on it: order them on one stream (or synchronise between them).  Each call
 // overwrites every partial it reads, so nothing has to start at zero.

@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -27,7 +28,6 @@ namespace ttns {
 #define NT 256
 #define NWARP (NT / 32)
 #define HBAR_EVFS 0.6582119569
-#define QR_NULL_REL 1e-8
 
 // status codes mirrored from ttns.h
 #define ST_TIMEOUT 5
@@ -1052,7 +1052,11 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
     pc.lap(P.ctl, 5);
     if (conv || m >= N || s_done == s_rem) break;
     s_rem -= s_done;
-    if (chunk == 63 && tm.rank == 0 && threadIdx.x == 0) atomicAdd(&P.ctl->not_converged, 1ull);
+    if (chunk == 63 && tm.rank == 0 && threadIdx.x == 0) {
+      // 64 Krylov spaces did not cover the time step: the result is incomplete
+      atomicAdd(&P.ctl->not_converged, 1ull);
+      set_status(P.ctl, ST_NOT_CONVERGED, I.op, I.node);
+    }
   }
   for (long long e = e0 + threadIdx.x; e < e1; e += NT) x[e] = Ks(0)[e - e0];
   if (tm.rank == 0 && threadIdx.x == 0) {
@@ -1196,6 +1200,268 @@ __device__ void tiled_pass(const KernelParams& P, Team& tm, const TiledApply& tp
   }
 }
 
+// ------------------------------------------------------------------ tensor-core apply
+// H_eff v for a node whose terms have at most one dense factor each (no dense x dense term):
+// the terms are grouped by the leg l their dense factor acts on, and every group is one complex
+// GEMM on the tensor cores,
+//   Y_l[r][i] = sum_{t in group, k} z_t[r][k] M_t[i][k],
+// with rows r = the node index with leg l removed, k the index of leg l, z_t = x with the
+// term's row-sparse factor (a, a^+, a diagonal or sparse pattern on another leg) applied while
+// the operand is staged, and M_t the term's dense matrix (an environment block or a dense
+// constant operator).  A task is one group and one tile of 128 rows; K is taken in chunks of at
+// most 32 complex values (64 real), so any leg dimension up to 64 fits the shared memory.  The
+// result of group g goes to its own compute-type buffer; the terms outside every group (a
+// row-sparse factor alone, or a dense factor on a leg below 8) stay on the SIMT path in the pass
+// that sums the groups (tc_sum_at).
+struct TcPlan {
+  int ok;
+  int ngroups;
+  int gleg[TTNS_MAX_LEGS];
+  int gfirst[TTNS_MAX_LEGS + 1];   // terms of group g: gterm[gfirst[g] .. gfirst[g + 1])
+  int gterm[TTNS_MAX_TERMS];
+  int gdense[TTNS_MAX_TERMS];      // index of the dense factor of each grouped term
+  int nsimt;
+  int simt[TTNS_MAX_TERMS];        // terms evaluated element-wise
+  int gtask0[TTNS_MAX_LEGS + 1];   // first task of group g (tasks of g: row tiles)
+  float inv_st[TTNS_MAX_LEGS];
+};
+__shared__ TcPlan s_tcp;
+
+struct TcState {
+  uint64_t mbar;
+  uint32_t tmem;
+  uint32_t phase;
+  int on;
+};
+__shared__ TcState s_tc;
+
+constexpr int kTcRows = 128;   // rows per task (the MMA's M)
+constexpr int kTcKc = 32;      // complex K per chunk
+constexpr int kTcTmemCols = 128;
+
+__device__ void tc_plan(const NodeDesc& nd, const OpStage& os, const TermList& L, TcPlan& tp) {
+  tp.ok = 0;
+  if (L.n2 > 0 || L.count > TTNS_MAX_TERMS) return;
+  int dleg[TTNS_MAX_TERMS], dfac[TTNS_MAX_TERMS];
+  for (int t = 0; t < L.count; ++t) {
+    const Term& T = os.terms[t];
+    dleg[t] = -1;
+    dfac[t] = -1;
+    if (T.nf == 1) {
+      if (T.f[0].nnz == 0 && nd.dims[T.f[0].leg] >= 8) { dleg[t] = T.f[0].leg; dfac[t] = 0; }
+    } else if (T.sparse_f >= 0) {
+      const int d = 1 - T.sparse_f;
+      if (T.f[d].nnz == 0 && nd.dims[T.f[d].leg] >= 8) { dleg[t] = T.f[d].leg; dfac[t] = d; }
+    }
+  }
+  tp.ngroups = 0;
+  tp.nsimt = 0;
+  int nt = 0, ntask = 0;
+  for (int l = 0; l < nd.nl; ++l) {
+    int c = 0;
+    for (int t = 0; t < L.count; ++t) c += dleg[t] == l;
+    if (c == 0) continue;
+    const int g = tp.ngroups++;
+    tp.gleg[g] = l;
+    tp.gfirst[g] = nt;
+    tp.gtask0[g] = ntask;
+    tp.inv_st[g] = 1.0f / (float)nd.strides[l];
+    for (int t = 0; t < L.count; ++t)
+      if (dleg[t] == l) { tp.gterm[nt] = t; tp.gdense[nt] = dfac[t]; ++nt; }
+    const int rows = nd.size / nd.dims[l];
+    ntask += (rows + kTcRows - 1) / kTcRows;
+  }
+  tp.gfirst[tp.ngroups] = nt;
+  tp.gtask0[tp.ngroups] = ntask;
+  for (int t = 0; t < L.count; ++t)
+    if (dleg[t] < 0) tp.simt[tp.nsimt++] = t;
+  tp.ok = tp.ngroups > 0;
+}
+
+// value of z = (row-sparse factor fs, if any) x at idx, in the compute type
+template <typename T, typename XT>
+__device__ __forceinline__ typename C2<T>::t tc_z(const KernelParams& P, const NodeDesc& nd, const Factor* fs,
+                                                  const XT* x, long long idx) {
+  if (!fs) return cvt<T>(x[idx]);
+  using V = typename C2<T>::t;
+  const LegPos lp = leg_pos(nd, fs->leg, idx);
+  const int D = nd.dims[fs->leg];
+  const double2* vals = P.pool + fs->sp + (long long)lp.i * fs->nnz;
+  const double2* cols = P.pool + fs->sp + (long long)D * fs->nnz + (long long)lp.i * fs->nnz;
+  V acc;
+  acc.x = acc.y = (T)0;
+  for (int e = 0; e < fs->nnz; ++e) {
+    const int k = (int)cols[e].x;
+    cmac<T>(acc, cvt<T>(vals[e]), cvt<T>(x[lp.base + (long long)k * nd.strides[fs->leg]]));
+  }
+  return acc;
+}
+
+// One task (group g, row tile rt): stages every chunk of the group's operands split for the
+// tensor cores, accumulates in TMEM, writes the tile's rows of Y_g.  Returns false if a
+// completion wait gave up (the status word is set).
+template <int KIND, typename T, typename XT>
+__device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage& os, const TcPlan& tp, int g, int rt,
+                        const XT* x, typename C2<T>::t* yg) {
+  using S = tc::Split<KIND>;
+  using V = typename C2<T>::t;
+  TcState& ts = s_tc;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int l = tp.gleg[g];
+  const int D = nd.dims[l];
+  const int st = nd.strides[l];
+  const int rows = nd.size / D;
+  const int r0 = rt * kTcRows;
+  const int Npad = ((2 * D + 15) / 16) * 16;
+  constexpr int G = 8 / S::esize;                 // complex values per 16-byte core row
+  const uint32_t kr_max = 2 * kTcKc;              // real K of a full chunk
+  const uint32_t a_plane = kTcRows * kr_max * S::esize;
+  const uint32_t b_plane = 128u * kr_max * S::esize;
+  unsigned char* A = dyn_smem;
+  unsigned char* B = dyn_smem + S::parts * a_plane;
+  bool first = true, ok = true;
+  for (int q = tp.gfirst[g]; q < tp.gfirst[g + 1] && ok; ++q) {
+    const Term& T_ = os.terms[tp.gterm[q]];
+    const Factor& fd = T_.f[tp.gdense[q]];
+    const Factor* fs = T_.nf == 2 ? &T_.f[1 - tp.gdense[q]] : nullptr;
+    const double2* M = P.pool + fd.mat;
+    for (int kb = 0; kb < D && ok; kb += kTcKc) {
+      const int kn = min(kTcKc, D - kb);                    // complex K of this chunk
+      const int Kr = ((2 * kn + 15) / 16) * 16;            // real K, padded to the MMA step
+      const int Kc = Kr / 2;
+      // A: rows of the tile, G consecutive complex k per thread (one 16-byte core row per plane)
+      for (int item = tid; item < kTcRows * (Kc / G); item += NT) {
+        const int row = item % kTcRows, kq = item / kTcRows;
+        const int R = r0 + row;
+        long long base = 0;
+        const bool in = R < rows;
+        if (in) {
+          const int outer = fdivu(R, st, tp.inv_st[g]);
+          base = (long long)outer * D * st + (R - outer * st);
+        }
+        float re[G], im[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int k = kq * G + j;
+          V z;
+          z.x = z.y = (T)0;
+          if (in && k < kn) z = tc_z<T>(P, nd, fs, x, base + (long long)(kb + k) * st);
+          re[j] = (float)z.x;
+          im[j] = (float)z.y;
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          tc::put_split_f<KIND>(A, a_plane, row, 2 * (kq * G + j), Kr, re[j]);
+          tc::put_split_f<KIND>(A, a_plane, row, 2 * (kq * G + j) + 1, Kr, im[j]);
+        }
+      }
+      // B: the 2 x 2 real blocks of M[i][kb + k]: rows 2i (a, -b) and 2i + 1 (b, a)
+      for (int item = tid; item < (Npad / 2) * (Kc / G); item += NT) {
+        const int kq = item % (Kc / G), i = item / (Kc / G);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int k = kq * G + j;
+          double2 m = make_double2(0.0, 0.0);
+          if (i < D && k < kn) m = M[(long long)i * D + kb + k];
+          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k, Kr, (float)m.x);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k + 1, Kr, (float)-m.y);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k, Kr, (float)m.y);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k + 1, Kr, (float)m.x);
+        }
+      }
+      tc::fence_proxy_async();
+      __syncthreads();
+      // planes are laid out for Kr columns: the descriptors use the chunk's own K
+      if (tid == 0) {
+        tc::fence_after();
+        tc::issue_chunk<KIND>(ts.tmem, A, a_plane, B, b_plane, Npad, Kr, !first);
+        tc::commit(&ts.mbar);
+      }
+      first = false;
+      const bool w = tc::mbar_wait(&ts.mbar, ts.phase, P.spin_limit);
+      tc::fence_after();
+      ok = __syncthreads_and(w) != 0;  // the same decision on every thread
+      if (tid == 0 && ok) ts.phase ^= 1u;
+      __syncthreads();
+    }
+  }
+  if (!ok) {
+    // a completion wait gave up: report it, give the MMAs in flight a last bounded wait, and
+    // leave the tensor cores alone in this CTA for the rest of the launch
+    if (tid == 0) set_status(P.ctl, ST_TIMEOUT, 400, -1);
+    tc::mbar_wait(&ts.mbar, ts.phase, P.spin_limit);
+    __syncthreads();
+    if (tid == 0) ts.on = 0;
+    __syncthreads();
+    return false;
+  }
+  // epilogue: accumulator row = TMEM lane; warps 0-3 own lanes 32 w .. 32 w + 31
+  if (warp < 4) {
+    const int R = r0 + warp * 32 + lane;
+    long long base = 0;
+    if (R < rows) {
+      const int outer = fdivu(R, st, tp.inv_st[g]);
+      base = (long long)outer * D * st + (R - outer * st);
+    }
+    for (int c0 = 0; c0 < Npad; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(ts.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (R < rows)
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const int i = (c0 + j) >> 1;
+          if (i < D) {
+            V y;
+            y.x = (T)v[j];
+            y.y = (T)v[j + 1];
+            yg[base + (long long)i * st] = y;
+          }
+        }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  return true;
+}
+
+// All tasks of the plan over the team's CTAs (task k on rank k mod size).  Y_g at
+// ybuf + g * ystride.  The caller synchronises the team before reading Y.
+template <typename T, typename XT>
+__device__ void tc_apply(const KernelParams& P, Team& tm, const NodeDesc& nd, const OpStage& os, const TcPlan& tp,
+                         const XT* x, typename C2<T>::t* ybuf, long long ystride) {
+  const int ntask = tp.gtask0[tp.ngroups];
+  for (int task = tm.rank; task < ntask; task += tm.size) {
+    int g = 0;
+    while (task >= tp.gtask0[g + 1]) ++g;
+    const int rt = task - tp.gtask0[g];
+    const bool ok = P.precision == 2 ? tc_task<tc::KIND_BF16X3, T>(P, nd, os, tp, g, rt, x, ybuf + g * ystride)
+                                     : tc_task<tc::KIND_TF32X3, T>(P, nd, os, tp, g, rt, x, ybuf + g * ystride);
+    if (!ok) break;
+  }
+}
+
+// H_eff x at idx from the group results and the terms left to the SIMT path
+template <typename T, typename XT>
+__device__ __forceinline__ typename C2<T>::t tc_sum_at(const KernelParams& P, const NodeDesc& nd, const OpStage& os,
+                                                      const TcPlan& tp, const XT* x,
+                                                      const typename C2<T>::t* ybuf, long long ystride,
+                                                      long long idx) {
+  typename C2<T>::t acc;
+  acc.x = acc.y = (T)0;
+  for (int g = 0; g < tp.ngroups; ++g) {
+    const auto y = ybuf[g * ystride + idx];
+    acc.x += y.x;
+    acc.y += y.y;
+  }
+  for (int q = 0; q < tp.nsimt; ++q) {
+    const Term& T_ = os.terms[tp.simt[q]];
+    const auto a = T_.nf == 1 ? factor_dot<T>(P, nd, T_.f[0], os, x, idx) : direct_dot<T>(P, nd, T_, os, x, idx);
+    acc.x += a.x;
+    acc.y += a.y;
+  }
+  return acc;
+}
+
 template <typename T>
 __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Instr& I, double2* work, double tau) {
   KrylovShared& ks = s_ks;
@@ -1213,7 +1479,22 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
   OpStage& os = s_os;
   stage_op<T>(P, I, L, nullptr, 0, os);
   using V = typename C2<T>::t;
-  V* xs = vec_smem<T>(P, os, N);  // input vector in shared memory when it fits
+  // tensor-core apply (split precision) for nodes whose terms have one dense factor each; its
+  // operand tiles take the dynamic shared memory, so nothing staged there is used
+  bool use_tc = false;
+  if (s_tc.on && (P.precision == 1 || P.precision == 2) && N >= 4096) {
+    if (threadIdx.x == 0) {
+      tc_plan(nd, os, L, s_tcp);
+      if (s_tcp.ok) {
+        os.a_n = os.b_n = 0;
+        os.end = 0;
+      }
+    }
+    __syncthreads();
+    use_tc = s_tcp.ok != 0;
+  }
+  V* ybuf = reinterpret_cast<V*>(work + (long long)(P.mmax + P.n_tmp + 2) * kv);  // group results (TC)
+  V* xs = use_tc ? nullptr : vec_smem<T>(P, os, N);  // input vector in shared memory when it fits
   // otherwise, in mixed precision, a compute-type copy of the input vector in the workspace,
   // written by the pass that produces the vector (FP64 Krylov basis, FP32 operand)
   constexpr bool kShadow = !std::is_same<T, double>::value;
@@ -1223,7 +1504,7 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
   TiledApply& tp = s_tp;
   V* xt = nullptr;
   bool tiled = false;
-  if (tm.kind == TEAM_GRID && xs == nullptr) {
+  if (tm.kind == TEAM_GRID && xs == nullptr && !use_tc) {
     if (threadIdx.x == 0) tiled_plan(nd, os, L, tp);
     __syncthreads();
     if (tp.ok) {
@@ -1299,7 +1580,12 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
           part[2] = fma(kj.x, kj.x, fma(kj.y, kj.y, part[2]));
         }
       };
-      if (tiled) {
+      if (use_tc) {
+        tc_apply<T>(P, tm, nd, os, s_tcp, xin, ybuf, kv);
+        team_sync(tm);
+        for (long long idx = tm.gtid(); idx < N; idx += tm.nthr())
+          recur(idx, tc_sum_at<T>(P, nd, os, s_tcp, xin, ybuf, kv, idx));
+      } else if (tiled) {
         V* y = tmp;  // pass A sums (no two-stage terms, so the temporaries are free)
         tiled_pass<T>(P, tm, tp, os, L, xin, xt, 0, [&](long long g, V acc) { y[g] = acc; });
         team_sync(tm);
@@ -1409,7 +1695,11 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
     pc.lap(P.ctl, 5);
     if (conv || m >= N || s_done == s_rem) break;
     s_rem -= s_done;
-    if (chunk == 63 && tm.rank == 0 && threadIdx.x == 0) atomicAdd(&P.ctl->not_converged, 1ull);
+    if (chunk == 63 && tm.rank == 0 && threadIdx.x == 0) {
+      // 64 Krylov spaces did not cover the time step: the result is incomplete
+      atomicAdd(&P.ctl->not_converged, 1ull);
+      set_status(P.ctl, ST_NOT_CONVERGED, I.op, I.node);
+    }
   }
   if (tm.rank == 0 && threadIdx.x == 0) {
     P.mhist[I.hist] = m;
@@ -1421,7 +1711,7 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
 
 // ------------------------------------------------------------------ Householder QR
 // A_v (matricised: rows = all other legs in order, columns = leg I.leg) = Q R with the
-// completion rule of the oracle: null sub-columns (norm <= 1e-8 ||M||_F) get the identity
+// completion rule of the oracle: null sub-columns (norm <= qr_cutoff ||M||_F) get the identity
 // reflector and R_jj = 0; Q = H_0 ... H_{n-1} I[:, :n] through the compact WY form
 // Q = I - V T V^H; finally R_jj is made real and >= 0.  FP64.
 struct QRShared {
@@ -1595,7 +1885,7 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     team_reduce_vec(tm, mine, redo, 4 * n + 1);
   }
   pc.lap(P.ctl, 8);
-  const double thr = QR_NULL_REL * sqrt(redo[4 * n]);
+  const double thr = P.qr_cutoff * sqrt(redo[4 * n]);
   for (int j = 0; j < n; ++j) {
     // reflector of column j: alpha = -phase(x0) sigma, vh = x0 - alpha = x0 (1 + sigma / |x0|),
     // |vh| = |x0| + sigma, |v|^2 = d_j + |vh|^2, tau = 2 / |v|^2.  Written so that the FP64
@@ -1608,12 +1898,14 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     double2 vh = make_double2(0, 0), alpha = make_double2(0, 0);
     const bool null = !(sigma > thr);
     if (!null) {
-      const double inv_ax = ax > 0.0 ? 1.0 / ax : 0.0;
+      // a head below 1e-280 counts as zero (phase 1): its reciprocal would overflow
+      const bool head = ax > 1e-280;
+      const double inv_ax = head ? 1.0 / ax : 0.0;
       const double hv = ax + sigma;
       const double vn2 = redo[0] + hv * hv;
       tau = 2.0 / vn2;
       shat = rsqrt(vn2);
-      if (ax > 0.0) {
+      if (head) {
         const double f = sigma * inv_ax;
         alpha = make_double2(-f * x0.x, -f * x0.y);
         vh = make_double2(x0.x + f * x0.x, x0.y + f * x0.y);
@@ -2065,10 +2357,31 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(KernelParams P, int phase) {
     if (threadIdx.x == 0 && blockIdx.x == 0) set_status(P.ctl, ST_LAUNCH, 300, (int)ncta);
     return;
   }
+  // tensor memory for the split-precision contractions (one 128-column accumulator per CTA)
+  const bool tc_on = P.precision == 1 || P.precision == 2;
+  if (threadIdx.x == 0) s_tc.on = 0;
+  if (tc_on) {
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&s_tc.tmem, kTcTmemCols);
+    if (threadIdx.x == 0) {
+      tc::mbar_init(&s_tc.mbar, 1);
+      s_tc.phase = 0;
+      s_tc.on = 1;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
+  __syncthreads();
   if (P.precision == 0)
     run<double>(P, phase);
   else
     run<float>(P, phase);
+  if (tc_on) {
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(s_tc.tmem, kTcTmemCols);
+  }
 }
 
 // ------------------------------------------------------------------ observables

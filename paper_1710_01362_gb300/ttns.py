@@ -16,16 +16,19 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libttns.so")
 
 TTNS_FP64 = 0
+TTNS_TF32X3 = 1
 TTNS_MIXED = 1
+TTNS_BF16X3 = 2
+TTNS_FP32 = 3
 
 STATUS = {0: "ok", 1: "invalid", 2: "oom", 3: "cuda", 4: "not converged", 5: "timeout", 6: "nonfinite", 7: "io"}
 
 EXPORTS = [
     "ttns_build_tree", "ttns_build_batch", "ttns_step", "ttns_sync", "ttns_reduced_density_matrix",
     "ttns_occupations", "ttns_observables", "ttns_trajectory", "ttns_populations_device", "ttns_get_counters",
-    "ttns_node_info", "ttns_get_node", "ttns_save", "ttns_load_state", "ttns_last_error", "ttns_free",
+    "ttns_node_info", "ttns_get_node", "ttns_save", "ttns_load", "ttns_load_state", "ttns_last_error", "ttns_free",
     "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan", "ttns_selftest_wait_timeout",
-    "ttns_rho_from_root_noalloc", "ttns_autotune",
+    "ttns_rho_from_root_noalloc", "ttns_autotune", "ttns_selftest_tc_gemm",
 ]
 
 
@@ -42,6 +45,7 @@ class Options(C.Structure):
         ("psi_el", C.POINTER(C.c_double)), ("record", C.c_int), ("max_record", C.c_int),
         ("cluster_ctas", C.c_int), ("grid_ctas", C.c_int), ("grid_threshold", C.c_int),
         ("spin_limit", C.c_longlong), ("profile", C.c_int), ("launch_flags", C.c_int),
+        ("qr_grid_threshold", C.c_int), ("qr_cutoff", C.c_double),
     ]
 
 
@@ -67,7 +71,7 @@ class Counters(C.Structure):
                 ("not_converged", C.c_longlong), ("steps", C.c_longlong), ("op_seconds", (C.c_double * 2) * 6),
                 ("op_count", (C.c_longlong * 2) * 6), ("expm_phase_seconds", C.c_double * 8),
                 ("qr_phase_seconds", C.c_double * 8), ("expm_phase_seconds_grid", C.c_double * 8),
-                ("qr_phase_seconds_grid", C.c_double * 8)]
+                ("qr_phase_seconds_grid", C.c_double * 8), ("launch_fallbacks", C.c_longlong)]
 
 
 _lib = None
@@ -98,10 +102,12 @@ def lib():
         L.ttns_get_node.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_size_t]
         L.ttns_save.argtypes = [C.c_void_p, C.c_char_p]
         L.ttns_load_state.argtypes = [C.c_void_p, C.c_char_p]
+        L.ttns_load.argtypes = [C.c_char_p, C.POINTER(Options), C.POINTER(C.c_void_p)]
         L.ttns_free.argtypes = [C.c_void_p]
         L.ttns_free.restype = None
         L.ttns_plan.argtypes = [C.c_int, C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(PlanInfo)]
         L.ttns_selftest_wait_timeout.argtypes = [C.c_longlong, C.POINTER(C.c_int)]
+        L.ttns_selftest_tc_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, C.POINTER(C.c_int)]
         L.ttns_rho_from_root_noalloc.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
         L.ttns_chain_ohmic.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp, dp]
         L.ttns_chain_from_modes.argtypes = [C.c_int, dp, dp, C.c_int, dp, dp, dp]
@@ -122,6 +128,19 @@ def selftest_wait_timeout(spin_limit: int) -> int:
     st = C.c_int(-1)
     _check(lib().ttns_selftest_wait_timeout(spin_limit, C.byref(st)))
     return st.value
+
+
+def selftest_tc_gemm(kind: int, Z: np.ndarray, Mt: np.ndarray):
+    """Y = Z Mt^T on the tensor cores (kind 1: TF32X3, 2: BF16X3); returns (Y, device status)."""
+    Zc = np.ascontiguousarray(Z, dtype=np.complex128)
+    Mc = np.ascontiguousarray(Mt, dtype=np.complex128)
+    M, K = Zc.shape
+    N = Mc.shape[0]
+    Y = np.zeros((M, N), dtype=np.complex128)
+    st = C.c_int(-1)
+    _check(lib().ttns_selftest_tc_gemm(kind, M, K, N, _dptr(Zc.view(np.float64)), _dptr(Mc.view(np.float64)),
+                                        _dptr(Y.view(np.float64)), C.byref(st)))
+    return Y, st.value
 
 
 def rho_from_root_noalloc(d_root: int, rows: int, n_el: int, d_rho: int, stream: Optional[int] = None) -> None:
@@ -175,7 +194,7 @@ class _ProblemKeep:
         self.om_ptrs = (C.POINTER(C.c_double) * len(self.om))(*[_dptr(x) for x in self.om])
         self.hop_ptrs = (C.POINTER(C.c_double) * len(self.hop))(*[_dptr(x) for x in self.hop])
         self.d = np.array([e.d for e in p.envs], dtype=np.int32)
-        self.D = np.array([min(e.D, 64) for e in p.envs], dtype=np.int32)
+        self.D = np.array([e.D for e in p.envs], dtype=np.int32)
         self.c = ProblemC(ne, _dptr(self.H), len(p.envs), _dptr(self.W), _dptr(self.rc),
                           self.L.ctypes.data_as(C.POINTER(C.c_int)), self.om_ptrs, self.hop_ptrs,
                           self.d.ctypes.data_as(C.POINTER(C.c_int)), self.D.ctypes.data_as(C.POINTER(C.c_int)))
@@ -193,7 +212,7 @@ def current_stream() -> Optional[int]:
 
 def _options(p0, precision, record=False, max_record=0, stream=None, cluster_ctas=0, grid_ctas=0,
              krylov_tol=0.0, krylov_mmax=0, keep=None, grid_threshold=0, spin_limit=0, profile=0,
-             launch_flags=0):
+             launch_flags=0, qr_grid_threshold=0, qr_cutoff=0.0):
     psi = None
     if p0.psi_el is not None:
         arr = _cplx(p0.psi_el)
@@ -202,15 +221,15 @@ def _options(p0, precision, record=False, max_record=0, stream=None, cluster_cta
         psi = _dptr(arr)
     return Options(precision, krylov_tol, krylov_mmax, stream, int(p0.er_tree), int(p0.D_er),
                    int(p0.init_state), psi, int(record), int(max_record), cluster_ctas, grid_ctas,
-                   grid_threshold, spin_limit, profile, launch_flags)
+                   grid_threshold, spin_limit, profile, launch_flags, qr_grid_threshold, qr_cutoff)
 
 
-def plan(problems, precision: int = TTNS_MIXED, krylov_mmax: int = 0) -> dict:
+def plan(problems, precision: int = TTNS_MIXED, krylov_mmax: int = 0, **kw) -> dict:
     """Host-only compile and table check; no GPU needed."""
     probs = list(problems) if isinstance(problems, (list, tuple)) else [problems]
     keep = [_ProblemKeep(p) for p in probs]
     hold = []
-    opt = _options(probs[0], precision, keep=hold, krylov_mmax=krylov_mmax)
+    opt = _options(probs[0], precision, keep=hold, krylov_mmax=krylov_mmax, **kw)
     arr = (ProblemC * len(probs))(*[k.c for k in keep])
     info = PlanInfo()
     _check(lib().ttns_plan(len(probs), arr, C.byref(opt), C.byref(info)))
@@ -222,7 +241,7 @@ def plan(problems, precision: int = TTNS_MIXED, krylov_mmax: int = 0) -> dict:
             "bonds": [info.bonds[i] for i in range(info.n_bonds_written)]}
 
 
-def autotune(problems, dt: float, precision: int = TTNS_MIXED, candidates=None, stream: Optional[int] = None):
+def autotune(problems, dt: float, precision: int = TTNS_MIXED, candidates=None, stream: Optional[int] = None, **kw):
     """Fastest number of CTAs per cluster team for this tree set (ttns_autotune); returns
     (cluster_ctas, seconds_per_step)."""
     probs = list(problems) if isinstance(problems, (list, tuple)) else [problems]
@@ -230,7 +249,7 @@ def autotune(problems, dt: float, precision: int = TTNS_MIXED, candidates=None, 
     hold = []
     if stream is None:
         stream = current_stream()
-    opt = _options(probs[0], precision, stream=stream, keep=hold)
+    opt = _options(probs[0], precision, stream=stream, keep=hold, **kw)
     arr = (ProblemC * len(probs))(*[k.c for k in keep])
     cand = list(candidates or [])
     carr = (C.c_int * max(1, len(cand)))(*cand) if cand else None
@@ -247,7 +266,7 @@ class Tree:
     def __init__(self, problems, precision: int = TTNS_MIXED, record: bool = False, max_record: int = 0,
                  stream: Optional[int] = None, cluster_ctas: int = 0, grid_ctas: int = 0,
                  krylov_tol: float = 0.0, krylov_mmax: int = 0, grid_threshold: int = 0, spin_limit: int = 0,
-                 profile: bool = False, launch_flags: int = 0):
+                 profile: bool = False, launch_flags: int = 0, qr_grid_threshold: int = 0, qr_cutoff: float = 0.0):
         single = not isinstance(problems, (list, tuple))
         probs = [problems] if single else list(problems)
         self.problems = probs
@@ -257,7 +276,8 @@ class Tree:
             stream = current_stream()
         self.opt = _options(probs[0], precision, record, max_record, stream, cluster_ctas, grid_ctas, krylov_tol,
                             krylov_mmax, keep=self._hold, grid_threshold=grid_threshold, spin_limit=spin_limit,
-                            profile=int(profile), launch_flags=int(launch_flags))
+                            profile=int(profile), launch_flags=int(launch_flags),
+                            qr_grid_threshold=qr_grid_threshold, qr_cutoff=qr_cutoff)
         h = C.c_void_p()
         arr = (ProblemC * len(probs))(*[k.c for k in self._keep])
         if len(probs) == 1:
@@ -333,7 +353,8 @@ class Tree:
         qr_g = dict(zip(qr_names, [c.qr_phase_seconds_grid[k] for k in range(8)]))
         return {"krylov_iters": c.krylov_iters, "applies": c.applies, "contraction_flops": c.contraction_flops,
                 "not_converged": c.not_converged, "steps": c.steps, "profile": prof, "expm_phases": phases,
-                "qr_phases": qr, "expm_phases_grid": phases_g, "qr_phases_grid": qr_g}
+                "qr_phases": qr, "expm_phases_grid": phases_g, "qr_phases_grid": qr_g,
+                "launch_fallbacks": c.launch_fallbacks}
 
     def n_nodes(self, k: int = 0) -> int:
         n = C.c_int()
@@ -355,3 +376,24 @@ class Tree:
 
     def load_state(self, path: str) -> None:
         _check(lib().ttns_load_state(self.h, path.encode()))
+
+    @classmethod
+    def load(cls, path: str, problems, precision: int = TTNS_MIXED, stream: Optional[int] = None,
+             **kw) -> "Tree":
+        """A new tree set built by ttns_load from a checkpoint file alone (problem, recording
+        settings and state come from the file).  `problems` gives the binding its host-side
+        shapes (electronic states and chain lengths) only."""
+        self = cls.__new__(cls)
+        probs = [problems] if not isinstance(problems, (list, tuple)) else list(problems)
+        self.problems = probs
+        self._keep = []
+        self._hold = []
+        if stream is None:
+            stream = current_stream()
+        self.opt = _options(probs[0], precision, stream=stream, keep=self._hold, **kw)
+        h = C.c_void_p()
+        self.h = None
+        _check(lib().ttns_load(path.encode(), C.byref(self.opt), C.byref(h)))
+        self.h = h
+        self.n_trees = len(probs)
+        return self

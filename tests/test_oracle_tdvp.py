@@ -43,6 +43,26 @@ def test_full_bond_dimension_is_exact_er_tree():
     np.testing.assert_allclose(st.rho_el(), ex.rho_el(psi), atol=1e-8)
 
 
+def test_energy_equals_the_dense_matrix_element_of_the_same_state():
+    # <H> from the centre tensor and the environment blocks (TTNS.energy) against
+    # <psi|H|psi> with psi = the oracle's own state contracted to a vector and H the dense
+    # matrix built directly from Eq. 2.  Both sides conserve energy, so a comparison with the
+    # exact trajectory's (constant) energy would only test t = 0, where the vacuum hides every
+    # coupling term; this compares the evaluation itself on entangled states.  A missing
+    # environment block, a dropped coupling channel or a wrong factor in H_eff(root) changes it.
+    cases = [W.ohmic_2state_L4(full_bond=True),
+             W.sf_small(seed=5, n_env=2, L=2, d=3, D=64, n_modes=4, dt=0.5, er_tree=True, D_er=64),
+             W.sf_small(seed=11, n_env=2, L=2, d=3, D=64, n_modes=4, dt=0.5),
+             W.sf_small(seed=11, n_env=2, L=3, d=3, D=4, n_modes=4, dt=0.5)]   # truncated bonds too
+    for p in cases:
+        st, ex = TTNS(p), Exact(p)
+        assert abs(st.energy() - ex.energy(ex.state(0.0))) < 1e-12
+        for k in range(6):
+            st.step(p.dt)
+            psi = st.to_dense()
+            assert abs(st.energy() - ex.energy(psi) / np.vdot(psi, psi).real) < 1e-12, (p.name, k)
+
+
 def test_zero_coupling_rabi_formula():
     p = W.rabi(eps=0.1, V=0.05, dt=0.5, n_steps=60)
     st = TTNS(p)

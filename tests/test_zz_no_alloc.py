@@ -43,3 +43,27 @@ def test_noalloc_density_matches_the_allocating_entry_point():
         ttns.rho_from_root_noalloc(d_root.data_ptr(), rows, 17, d_rho.data_ptr(), stream)
     assert e.value.code == 1
     g.close()
+
+
+def test_noalloc_density_at_the_scratch_limits():
+    # rows = 20000, n_el = 16: 256 blocks of 16 x 16 partials, the whole fixed scratch array,
+    # against a plain einsum on the host; then a size at the 2^24 element limit is rejected
+    # before anything is launched
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    rng = np.random.default_rng(5)
+    rows, n_el = 20000, 16
+    A = (rng.standard_normal((rows, n_el)) + 1j * rng.standard_normal((rows, n_el))) / np.sqrt(rows)
+    ref = np.einsum("rs,rt->st", A, A.conj())
+    stream = torch.cuda.current_stream().cuda_stream
+    d_root = torch.from_numpy(np.ascontiguousarray(A).view(np.float64).reshape(-1)).cuda()
+    for call in range(2):
+        d_rho = torch.full((2 * n_el * n_el,), float("nan"), dtype=torch.float64, device="cuda")
+        ttns.rho_from_root_noalloc(d_root.data_ptr(), rows, n_el, d_rho.data_ptr(), stream)
+        torch.cuda.synchronize()
+        got = d_rho.cpu().numpy().view(np.complex128).reshape(n_el, n_el)
+        assert np.abs(got - ref).max() < 1e-12, f"call {call}"
+    with pytest.raises(ttns.TTNSError) as e:
+        ttns.rho_from_root_noalloc(d_root.data_ptr(), (1 << 24) // n_el, n_el, d_rho.data_ptr(), stream)
+    assert e.value.code == 1
