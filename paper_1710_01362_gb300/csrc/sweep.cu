@@ -1236,8 +1236,7 @@ struct TcState {
 __shared__ TcState s_tc;
 
 constexpr int kTcRows = 128;   // rows per task (the MMA's M)
-constexpr int kTcKc = 32;      // complex K per chunk
-constexpr int kTcTmemCols = 128;
+constexpr int kTcTmemCols = 512;  // all of an SM's tensor memory (one CTA per SM)
 
 __device__ void tc_plan(const NodeDesc& nd, const OpStage& os, const TermList& L, TcPlan& tp) {
   tp.ok = 0;
@@ -1297,9 +1296,13 @@ __device__ __forceinline__ typename C2<T>::t tc_z(const KernelParams& P, const N
   return acc;
 }
 
-// One task (group g, row tile rt): stages every chunk of the group's operands split for the
-// tensor cores, accumulates in TMEM, writes the tile's rows of Y_g.  Returns false if a
-// completion wait gave up (the status word is set).
+// One task (group g, row tile rt).  K runs over (term, leg index) of the group's terms back to
+// back; it is staged in chunks of n_acc MMA K steps, every K step accumulates into its own TMEM
+// columns (the tensor core's accumulation rounds toward zero, so a long accumulation drifts),
+// and the steps are summed in shared memory in FP32 round-to-nearest, in a fixed order.  The
+// operand loads of a thread are issued together (four items at a time) before any is
+// converted, so their latencies overlap.  Returns false if a completion wait gave up (the
+// status word is set).
 template <int KIND, typename T, typename XT>
 __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage& os, const TcPlan& tp, int g, int rt,
                         const XT* x, typename C2<T>::t* yg) {
@@ -1313,77 +1316,133 @@ __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage
   const int rows = nd.size / D;
   const int r0 = rt * kTcRows;
   const int Npad = ((2 * D + 15) / 16) * 16;
-  constexpr int G = 8 / S::esize;                 // complex values per 16-byte core row
-  const uint32_t kr_max = 2 * kTcKc;              // real K of a full chunk
-  const uint32_t a_plane = kTcRows * kr_max * S::esize;
-  const uint32_t b_plane = 128u * kr_max * S::esize;
-  unsigned char* A = dyn_smem;
-  unsigned char* B = dyn_smem + S::parts * a_plane;
-  bool first = true, ok = true;
-  for (int q = tp.gfirst[g]; q < tp.gfirst[g + 1] && ok; ++q) {
-    const Term& T_ = os.terms[tp.gterm[q]];
-    const Factor& fd = T_.f[tp.gdense[q]];
-    const Factor* fs = T_.nf == 2 ? &T_.f[1 - tp.gdense[q]] : nullptr;
-    const double2* M = P.pool + fd.mat;
-    for (int kb = 0; kb < D && ok; kb += kTcKc) {
-      const int kn = min(kTcKc, D - kb);                    // complex K of this chunk
-      const int Kr = ((2 * kn + 15) / 16) * 16;            // real K, padded to the MMA step
-      const int Kc = Kr / 2;
-      // A: rows of the tile, G consecutive complex k per thread (one 16-byte core row per plane)
-      for (int item = tid; item < kTcRows * (Kc / G); item += NT) {
-        const int row = item % kTcRows, kq = item / kTcRows;
-        const int R = r0 + row;
-        long long base = 0;
-        const bool in = R < rows;
-        if (in) {
-          const int outer = fdivu(R, st, tp.inv_st[g]);
-          base = (long long)outer * D * st + (R - outer * st);
-        }
-        float re[G], im[G];
+  const int nterm = tp.gfirst[g + 1] - tp.gfirst[g];
+  constexpr int G = 8 / S::esize;                // complex values per 16-byte core row
+  constexpr int KSC = S::kstep / 2;              // complex K per MMA K step
+  const int n_acc = min(8, kTcTmemCols / Npad);   // K steps per chunk, one TMEM slot each
+  const int chunk_kc = n_acc * KSC;
+  const int ktot = ((nterm * D + KSC - 1) / KSC) * KSC;
+  const int ldsum = Npad + 1;
+  float* sums = reinterpret_cast<float*>(dyn_smem);
+  const uint32_t a_plane = (uint32_t)kTcRows * 2 * chunk_kc * S::esize;
+  const uint32_t b_plane = (uint32_t)Npad * 2 * chunk_kc * S::esize;
+  const uint32_t sum_bytes = ((uint32_t)kTcRows * ldsum * 4u + 1023u) & ~1023u;
+  unsigned char* A = dyn_smem + sum_bytes;
+  unsigned char* B = A + S::parts * a_plane;
+  // this thread's share of the accumulator: row (TMEM lane) and half of the columns
+  const int q4 = warp & 3, half = warp >> 2;
+  const int my_row = q4 * 32 + lane;
+  const int c_lo = half * (Npad / 2), c_hi = c_lo + Npad / 2;
+  for (int c = c_lo; c < c_hi; ++c) sums[my_row * ldsum + c] = 0.0f;
+  bool ok = true;
+  for (int kc0 = 0; kc0 < ktot && ok; kc0 += chunk_kc) {
+    const int nk = min(chunk_kc, ktot - kc0);   // a multiple of KSC
+    const int Kr = 2 * nk;
+    // A: rows of the tile x (term, k) of the chunk
+    {
+      const int per_row = nk / G;
+      const int nitems = kTcRows * per_row;
+      for (int it0 = tid; it0 < nitems; it0 += 4 * NT) {
+        float re[4][G], im[4][G];
 #pragma unroll
-        for (int j = 0; j < G; ++j) {
-          const int k = kq * G + j;
-          V z;
-          z.x = z.y = (T)0;
-          if (in && k < kn) z = tc_z<T>(P, nd, fs, x, base + (long long)(kb + k) * st);
-          re[j] = (float)z.x;
-          im[j] = (float)z.y;
+        for (int u = 0; u < 4; ++u) {
+          const int item = it0 + u * NT;
+          const int row = item % kTcRows, kq = item / kTcRows;
+          const int R = r0 + row;
+          const bool in = item < nitems && R < rows;
+          long long base = 0;
+          if (in) {
+            const int outer = fdivu(R, st, tp.inv_st[g]);
+            base = (long long)outer * D * st + (R - outer * st);
+          }
+#pragma unroll
+          for (int j = 0; j < G; ++j) {
+            const int kg = kc0 + kq * G + j;   // global K index: term kg / D, leg index kg % D
+            V z;
+            z.x = z.y = (T)0;
+            if (in && kg < nterm * D) {
+              const int tl = kg / D, kk = kg - tl * D;
+              const int q = tp.gfirst[g] + tl;
+              const Term& T_ = os.terms[tp.gterm[q]];
+              const Factor* fs = T_.nf == 2 ? &T_.f[1 - tp.gdense[q]] : nullptr;
+              z = tc_z<T>(P, nd, fs, x, base + (long long)kk * st);
+            }
+            re[u][j] = (float)z.x;
+            im[u][j] = (float)z.y;
+          }
         }
 #pragma unroll
-        for (int j = 0; j < G; ++j) {
-          tc::put_split_f<KIND>(A, a_plane, row, 2 * (kq * G + j), Kr, re[j]);
-          tc::put_split_f<KIND>(A, a_plane, row, 2 * (kq * G + j) + 1, Kr, im[j]);
+        for (int u = 0; u < 4; ++u) {
+          const int item = it0 + u * NT;
+          if (item >= nitems) break;
+          const int row = item % kTcRows, kq = item / kTcRows;
+#pragma unroll
+          for (int j = 0; j < G; ++j) {
+            tc::put_split_f<KIND>(A, a_plane, row, 2 * (kq * G + j), Kr, re[u][j]);
+            tc::put_split_f<KIND>(A, a_plane, row, 2 * (kq * G + j) + 1, Kr, im[u][j]);
+          }
         }
       }
-      // B: the 2 x 2 real blocks of M[i][kb + k]: rows 2i (a, -b) and 2i + 1 (b, a)
-      for (int item = tid; item < (Npad / 2) * (Kc / G); item += NT) {
-        const int kq = item % (Kc / G), i = item / (Kc / G);
-#pragma unroll
-        for (int j = 0; j < G; ++j) {
-          const int k = kq * G + j;
-          double2 m = make_double2(0.0, 0.0);
-          if (i < D && k < kn) m = M[(long long)i * D + kb + k];
-          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k, Kr, (float)m.x);
-          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k + 1, Kr, (float)-m.y);
-          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k, Kr, (float)m.y);
-          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k + 1, Kr, (float)m.x);
-        }
-      }
-      tc::fence_proxy_async();
-      __syncthreads();
-      // planes are laid out for Kr columns: the descriptors use the chunk's own K
-      if (tid == 0) {
-        tc::fence_after();
-        tc::issue_chunk<KIND>(ts.tmem, A, a_plane, B, b_plane, Npad, Kr, !first);
-        tc::commit(&ts.mbar);
-      }
-      first = false;
-      const bool w = tc::mbar_wait(&ts.mbar, ts.phase, P.spin_limit);
-      tc::fence_after();
-      ok = __syncthreads_and(w) != 0;  // the same decision on every thread
-      if (tid == 0 && ok) ts.phase ^= 1u;
-      __syncthreads();
     }
+    // B: the 2 x 2 real blocks of M_t[i][k]: rows 2i (a, -b) and 2i + 1 (b, a)
+    {
+      const int per_i = nk / G;
+      const int nitems = (Npad / 2) * per_i;
+      for (int item = tid; item < nitems; item += NT) {
+        const int kq = item % per_i, i = item / per_i;
+        double2 m[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int kg = kc0 + kq * G + j;
+          m[j] = make_double2(0.0, 0.0);
+          if (i < D && kg < nterm * D) {
+            const int tl = kg / D, kk = kg - tl * D;
+            const int q = tp.gfirst[g] + tl;
+            const Factor& fd = os.terms[tp.gterm[q]].f[tp.gdense[q]];
+            m[j] = P.pool[fd.mat + (long long)i * D + kk];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+          const int k = kq * G + j;
+          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k, Kr, (float)m[j].x);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k + 1, Kr, (float)-m[j].y);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k, Kr, (float)m[j].y);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k + 1, Kr, (float)m[j].x);
+        }
+      }
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    const int nsteps = nk / KSC;
+    if (tid == 0) {
+      tc::fence_after();
+      for (int ks = 0; ks < nsteps; ++ks)
+        tc::issue_kstep<KIND>(ts.tmem + (uint32_t)(ks * Npad), A, a_plane, B, b_plane, Npad, Kr, ks);
+      tc::commit(&ts.mbar);
+    }
+    const bool w = tc::mbar_wait(&ts.mbar, ts.phase, P.spin_limit);
+    tc::fence_after();
+    ok = __syncthreads_and(w) != 0;  // the same decision on every thread
+    if (!ok) break;
+    if (tid == 0) ts.phase ^= 1u;
+    // the K steps' partial products, summed in a fixed order into the shared FP32 sums
+    const uint32_t lane_base = ts.tmem + ((uint32_t)(q4 * 32) << 16);
+    for (int c = c_lo; c < c_hi; c += 8) {
+      float acc[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+      for (int ks = 0; ks < nsteps; ++ks) {
+        float v[8];
+        tc::tmem_ld8(lane_base + (uint32_t)(ks * Npad + c), v);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += v[j];
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) sums[my_row * ldsum + c + j] += acc[j];
+    }
+    tc::fence_before();
+    __syncthreads();
   }
   if (!ok) {
     // a completion wait gave up: report it, give the MMAs in flight a last bounded wait, and
@@ -1395,31 +1454,21 @@ __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage
     __syncthreads();
     return false;
   }
-  // epilogue: accumulator row = TMEM lane; warps 0-3 own lanes 32 w .. 32 w + 31
-  if (warp < 4) {
-    const int R = r0 + warp * 32 + lane;
-    long long base = 0;
-    if (R < rows) {
-      const int outer = fdivu(R, st, tp.inv_st[g]);
-      base = (long long)outer * D * st + (R - outer * st);
-    }
-    for (int c0 = 0; c0 < Npad; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(ts.tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (R < rows)
-#pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          const int i = (c0 + j) >> 1;
-          if (i < D) {
-            V y;
-            y.x = (T)v[j];
-            y.y = (T)v[j + 1];
-            yg[base + (long long)i * st] = y;
-          }
-        }
+  // the tile's rows of Y_g: row R = (outer, inner) of leg l, column pair (2i, 2i + 1) = y[.., i, ..]
+  const int R = r0 + my_row;
+  if (R < rows) {
+    const int outer = fdivu(R, st, tp.inv_st[g]);
+    const long long base = (long long)outer * D * st + (R - outer * st);
+    for (int c = c_lo; c < c_hi; c += 2) {
+      const int i = c >> 1;
+      if (i < D) {
+        V y;
+        y.x = (T)sums[my_row * ldsum + c];
+        y.y = (T)sums[my_row * ldsum + c + 1];
+        yg[base + (long long)i * st] = y;
+      }
     }
   }
-  tc::fence_before();
   __syncthreads();
   return true;
 }

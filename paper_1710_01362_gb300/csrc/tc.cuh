@@ -112,6 +112,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // ---------------------------------------------------------------- operand split and layout
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
@@ -200,6 +210,40 @@ __device__ __forceinline__ void issue_chunk(uint32_t d_tmem, const unsigned char
         mma_f16(d_tmem, da, db, id, first ? 0u : 1u);
       first = false;
     }
+  }
+}
+
+// Issues the split products of one MMA K step (k-step index ks of the staged chunk) into a
+// fresh accumulator at column d_tmem: the small products first, the hi*hi product last, so that
+// the accumulator is rounded once at full scale.  The tensor core rounds its FP32 accumulation
+// toward zero (measured on GB300: about -0.4 ulp per MMA instruction); one full-scale rounding
+// per K step, with the steps summed on the CUDA cores in round-to-nearest, keeps the sum within
+// the FP32 level instead of drifting by 0.4 ulp per instruction.
+template <int KIND>
+__device__ __forceinline__ void issue_kstep(uint32_t d_tmem, const unsigned char* A, uint32_t a_plane,
+                                            const unsigned char* B, uint32_t b_plane, int N, int K, int ks) {
+  using S = Split<KIND>;
+  const uint32_t E = 16 / S::esize;
+  const uint32_t sbo = 128u * (uint32_t)(K / (int)E);
+  const uint32_t id = idesc(KIND == KIND_TF32X3 ? 2u : 1u, 128, N);
+  const uint32_t koff = (uint32_t)(ks * S::kstep / (int)E) * 128u;
+  const uint32_t a0 = smem_u32(A) + koff, b0 = smem_u32(B) + koff;
+  // products ordered from the smallest scale to the largest:
+  //   TF32X3 (planes h = 0, l = 1): l*h, h*l, h*h
+  //   BF16X3 (planes 0, 1, 2):      2*0, 1*1, 0*2, 1*0, 0*1, 0*0
+  constexpr int NP = KIND == KIND_TF32X3 ? 3 : 6;
+  constexpr int tf_a[3] = {1, 0, 0}, tf_b[3] = {0, 1, 0};
+  constexpr int bf_a[6] = {2, 1, 0, 1, 0, 0}, bf_b[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const int pa = KIND == KIND_TF32X3 ? tf_a[q] : bf_a[q];
+    const int pb = KIND == KIND_TF32X3 ? tf_b[q] : bf_b[q];
+    const uint64_t da = sdesc(a0 + pa * a_plane, 128, sbo);
+    const uint64_t db = sdesc(b0 + pb * b_plane, 128, sbo);
+    if constexpr (KIND == KIND_TF32X3)
+      mma_tf32(d_tmem, da, db, id, q == 0 ? 0u : 1u);
+    else
+      mma_f16(d_tmem, da, db, id, q == 0 ? 0u : 1u);
   }
 }
 

@@ -4,6 +4,7 @@
 // host.  The paper has no counterpart: this checks this library's own building block.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <string>
 
 #include "../../include/ttns.h"
@@ -14,10 +15,12 @@ namespace ttns {
 void set_last_error(const std::string& msg);
 
 namespace {
-constexpr int kKC = 32;       // complex K per chunk (64 real)
 constexpr int kNT = 256;
-constexpr int kTmemCols = 256;
+constexpr int kTmemCols = 512;
 
+// Y = Z Mt^T for one CTA, with the sweep's accumulation scheme: chunks of n_acc MMA K steps,
+// one fresh TMEM accumulator per K step (small split products first, hi * hi last), and the
+// K steps summed on the CUDA cores in FP32 round-to-nearest in a fixed order.
 template <int KIND>
 __global__ void __launch_bounds__(kNT, 1)
     k_tc_selftest(const double2* Z, const double2* Mt, double2* Y, int Mrows, int Kc, int Nc, int* status,
@@ -27,33 +30,43 @@ __global__ void __launch_bounds__(kNT, 1)
   __shared__ uint64_t mbar;
   __shared__ uint32_t tbase_s;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int Kr = 2 * kKC;                       // real K of one chunk
   const int Npad = ((2 * Nc + 15) / 16) * 16;   // real N, a multiple of 16 (M = 128)
-  const uint32_t a_plane = 128u * Kr * S::esize;
-  const uint32_t b_plane = (uint32_t)Npad * Kr * S::esize;
-  unsigned char* A = sm;
-  unsigned char* B = sm + S::parts * a_plane;
+  constexpr int KSC = S::kstep / 2;              // complex K per MMA K step
+  const int n_acc = min(8, kTmemCols / Npad);
+  const int chunk_kc = n_acc * KSC;
+  const int ktot = ((Kc + KSC - 1) / KSC) * KSC;
+  const int ldsum = Npad + 1;
+  float* sums = reinterpret_cast<float*>(sm);
+  const uint32_t sum_bytes = ((uint32_t)128 * ldsum * 4u + 1023u) & ~1023u;
+  const uint32_t a_plane = 128u * 2 * chunk_kc * S::esize;
+  const uint32_t b_plane = (uint32_t)Npad * 2 * chunk_kc * S::esize;
+  unsigned char* A = sm + sum_bytes;
+  unsigned char* B = A + S::parts * a_plane;
   if (warp == 0) tc::tmem_alloc(&tbase_s, kTmemCols);
   if (tid == 0) tc::mbar_init(&mbar, 1);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = tbase_s;
+  const int q4 = warp & 3, half = warp >> 2, my_row = q4 * 32 + lane;
+  const int c_lo = half * (Npad / 2), c_hi = c_lo + Npad / 2;
   uint32_t phase = 0;
   bool ok = true;
   for (int row0 = 0; row0 < Mrows && ok; row0 += 128) {
-    for (int kc0 = 0; kc0 < Kc && ok; kc0 += kKC) {
-      // A chunk: rows row0.., complex k -> real columns 2k (re), 2k + 1 (im)
-      for (int idx = tid; idx < 128 * kKC; idx += kNT) {
-        const int r = idx / kKC, k = idx % kKC;
+    for (int c = c_lo; c < c_hi; ++c) sums[my_row * ldsum + c] = 0.0f;
+    for (int kc0 = 0; kc0 < ktot && ok; kc0 += chunk_kc) {
+      const int nk = min(chunk_kc, ktot - kc0);
+      const int Kr = 2 * nk;
+      for (int idx = tid; idx < 128 * nk; idx += kNT) {
+        const int r = idx % 128, k = idx / 128;
         double2 z = make_double2(0.0, 0.0);
         if (row0 + r < Mrows && kc0 + k < Kc) z = Z[(long long)(row0 + r) * Kc + kc0 + k];
         tc::put_split<KIND>(A, a_plane, r, 2 * k, Kr, z.x);
         tc::put_split<KIND>(A, a_plane, r, 2 * k + 1, Kr, z.y);
       }
-      // B chunk: 2 x 2 real blocks of M[i][k] = a + ib: [[a, -b], [b, a]]
-      for (int idx = tid; idx < (Npad / 2) * kKC; idx += kNT) {
-        const int i = idx / kKC, k = idx % kKC;
+      // 2 x 2 real blocks of M[i][k] = a + ib: [[a, -b], [b, a]]
+      for (int idx = tid; idx < (Npad / 2) * nk; idx += kNT) {
+        const int k = idx % nk, i = idx / nk;
         double2 m = make_double2(0.0, 0.0);
         if (i < Nc && kc0 + k < Kc) m = Mt[(long long)i * Kc + kc0 + k];
         tc::put_split<KIND>(B, b_plane, 2 * i, 2 * k, Kr, m.x);
@@ -63,41 +76,52 @@ __global__ void __launch_bounds__(kNT, 1)
       }
       tc::fence_proxy_async();
       __syncthreads();
+      const int nsteps = nk / KSC;
       if (tid == 0) {
         tc::fence_after();
-        tc::issue_chunk<KIND>(tbase, A, a_plane, B, b_plane, Npad, Kr, kc0 > 0);
+        for (int ks = 0; ks < nsteps; ++ks)
+          tc::issue_kstep<KIND>(tbase + (uint32_t)(ks * Npad), A, a_plane, B, b_plane, Npad, Kr, ks);
         tc::commit(&mbar);
       }
-      ok = tc::mbar_wait(&mbar, phase, spin_limit);
-      phase ^= 1u;
+      const bool w = tc::mbar_wait(&mbar, phase, spin_limit);
       tc::fence_after();
+      ok = __syncthreads_and(w) != 0;
+      if (!ok) break;
+      phase ^= 1u;
+      const uint32_t lane_base = tbase + ((uint32_t)(q4 * 32) << 16);
+      for (int c = c_lo; c < c_hi; c += 8) {
+        float acc[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
+        for (int ks = 0; ks < nsteps; ++ks) {
+          float v[8];
+          tc::tmem_ld8(lane_base + (uint32_t)(ks * Npad + c), v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[j] += v[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sums[my_row * ldsum + c + j] += acc[j];
+      }
+      tc::fence_before();
       __syncthreads();
     }
     if (!ok) break;
-    // epilogue: warps 0-3 read their 32 accumulator rows, 16 columns at a time
-    if (warp < 4) {
-      const int r = row0 + warp * 32 + lane;
-      for (int c0 = 0; c0 < Npad; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (r < Mrows)
-#pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            const int i = (c0 + j) >> 1;
-            if (i < Nc) Y[(long long)r * Nc + i] = make_double2((double)v[j], (double)v[j + 1]);
-          }
+    const int r = row0 + my_row;
+    if (r < Mrows)
+      for (int c = c_lo; c < c_hi; c += 2) {
+        const int i = c >> 1;
+        if (i < Nc) Y[(long long)r * Nc + i] = make_double2((double)sums[my_row * ldsum + c], (double)sums[my_row * ldsum + c + 1]);
       }
-    }
-    tc::fence_before();
     __syncthreads();
-    tc::fence_after();
   }
   if (!ok) {
     if (tid == 0) atomicCAS(status, 0, (int)TTNS_E_TIMEOUT);
     // the MMAs may still be running: wait once more (bounded) before the TMEM is released
-    tc::mbar_wait(&mbar, phase ^ 1u, spin_limit);
+    tc::mbar_wait(&mbar, phase, spin_limit);
   }
+  tc::fence_before();
   __syncthreads();
+  tc::fence_after();
   if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
@@ -105,7 +129,10 @@ template <int KIND>
 cudaError_t launch_selftest(const double2* Z, const double2* Mt, double2* Y, int M, int K, int N, int* st) {
   using S = tc::Split<KIND>;
   const int Npad = ((2 * N + 15) / 16) * 16;
-  const size_t smem = (size_t)S::parts * (128 + Npad) * (2 * kKC) * S::esize;
+  const int n_acc = std::min(8, kTmemCols / Npad);
+  const int chunk_kc = n_acc * (S::kstep / 2);
+  const size_t sum_bytes = ((size_t)128 * (Npad + 1) * 4 + 1023) & ~(size_t)1023;
+  const size_t smem = sum_bytes + (size_t)S::parts * (128 + Npad) * (2 * chunk_kc) * S::esize;
   cudaError_t e = cudaFuncSetAttribute(k_tc_selftest<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_tc_selftest<KIND><<<1, kNT, smem>>>(Z, Mt, Y, M, K, N, st, 4000000000LL);

@@ -8,6 +8,13 @@ order 2^-24 and below.  FP32 accumulation over K <= 2 x 160 real terms adds at m
 a few 1e-6 in the worst case.  A single TF32 or BF16 product (5e-4 / 4e-3 relative),
 a dropped cross term, a wrong operand layout or a wrong sign in the 2 x 2 blocks all
 fail this bound by orders of magnitude.
+
+Drift: the tensor core rounds its FP32 accumulation toward zero (about -0.4 ulp per MMA
+instruction, measured on GB300), so one accumulator carried over K = 1024 complex
+(768 instructions) shrinks a sum of positive products by 1.7e-5.  The tile gives every MMA
+K step its own accumulator and sums the steps in round-to-nearest: the mean signed error
+over positive data must stay below 1e-7 (one full-scale truncation per step, unbiased
+summation).
 """
 import numpy as np
 import pytest
@@ -52,3 +59,17 @@ def test_tc_gemm_scales_and_signs():
         ref = Z @ Mt.T
         scale = np.abs(Z) @ np.abs(Mt).T
         assert (np.abs(Y - ref) / scale).max() < 4e-6
+
+
+@pytest.mark.parametrize("kind", [1, 2])
+def test_tc_gemm_has_no_accumulation_drift(kind):
+    rng = np.random.default_rng(11 + kind)
+    for K in (64, 1024):
+        Z = rng.uniform(0.5, 1.0, (256, K)) + 0j
+        Mt = rng.uniform(0.5, 1.0, (16, K)) + 0j
+        Y, st = ttns.selftest_tc_gemm(kind, Z, Mt)
+        assert st == 0
+        ref = (Z @ Mt.T).real
+        rel = (Y.real - ref) / ref
+        assert abs(rel.mean()) < 1e-7, f"K={K}: mean signed error {rel.mean():.2e}"
+        assert np.abs(rel).max() < 1e-6, f"K={K}: max error {np.abs(rel).max():.2e}"
