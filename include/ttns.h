@@ -271,6 +271,35 @@ ttns_status ttns_selftest_wait_timeout(long long spin_limit, int* device_status)
 ttns_status ttns_selftest_tc_gemm(int kind, int M, int K, int N, const double* Z, const double* Mt, double* Y,
                                   int* device_status);
 
+/* Surrogate-network kernels (no counterpart in the paper, which names machine learning
+ * among the advances its method builds on (Introduction) but gives no network: these train
+ * and run this library's multilayer perceptron from Hamiltonian parameters to population
+ * trajectories, with the TTNS sweep as its fallback).  All pointers are caller-owned device
+ * memory (FP32, row-major); every call is enqueued on cuda_stream (NULL = legacy default
+ * stream), allocates nothing and does not synchronise.
+ *
+ * ttns_mlp_gemm: C = op(A) op(B) on the tensor cores (tcgen05), M x N, inner dimension K,
+ *   op(A)(m, k) = transA ? A[k * lda + m] : A[m * lda + k],
+ *   op(B)(k, n) = transB ? B[n * ldb + k] : B[k * ldb + n],
+ *   kind 1: 3xTF32 products (FP32-level, for training); kind 3: one BF16 product (inference).
+ *   Every MMA K step has its own tensor-memory accumulator and the steps are summed in FP32
+ *   round-to-nearest.  epilogue: 0 C = AB; 1 C = AB + aux[n] (bias); 2 C = tanh(AB + aux[n]);
+ *   3 C = AB * (1 - aux[m * ldc + n]^2) (backward through tanh, aux = that layer's output).
+ * ttns_mlp_colsum: out[n] = sum_m X[m * ld + n] (bias gradients), fixed order.
+ * ttns_mlp_diff:   dy[i] = (y[i] - t[i]) * scale (gradient of the squared loss).
+ * ttns_mlp_adam:   one Adam step (Kingma & Ba) on n parameters p with gradients g and moments
+ *   m, v at step number step >= 1.
+ * ttns_mlp_status: synchronises the device and reads the status word of the layer products
+ *   (TTNS_E_TIMEOUT if a completion wait gave up), clearing it when clear != 0.
+ * Bad sizes or NULL pointers give TTNS_E_INVALID before anything is launched. */
+ttns_status ttns_mlp_gemm(int kind, int M, int N, int K, const float* A, int lda, int transA, const float* B, int ldb,
+                          int transB, float* C, int ldc, int epilogue, const float* aux, void* cuda_stream);
+ttns_status ttns_mlp_colsum(const float* X, int M, int N, int ld, float* out, void* cuda_stream);
+ttns_status ttns_mlp_diff(const float* y, const float* t, float* dy, long long n, float scale, void* cuda_stream);
+ttns_status ttns_mlp_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float beta1, float beta2,
+                          float eps, int step, void* cuda_stream);
+ttns_status ttns_mlp_status(int* device_status, int clear);
+
 /* Electronic reduced density matrix from a root tensor in caller-owned device
  * memory, allocating nothing (the paper has no counterpart: this is for callers
  * that cannot call cudaMalloc, e.g. code running inside another framework's

@@ -27,7 +27,7 @@
 namespace ttns {
 namespace tc {
 
-enum Kind : int { KIND_TF32X3 = 1, KIND_BF16X3 = 2 };
+enum Kind : int { KIND_TF32X3 = 1, KIND_BF16X3 = 2, KIND_BF16X1 = 3 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -160,7 +160,9 @@ __device__ __forceinline__ void put_split(unsigned char* base, uint32_t pstride,
 }
 template <int KIND>
 __device__ __forceinline__ void put_split_f(unsigned char* base, uint32_t pstride, int row, int k, int K, float x) {
-  if constexpr (KIND == KIND_TF32X3) {
+  if constexpr (KIND == KIND_BF16X1) {
+    *reinterpret_cast<__nv_bfloat16*>(base + kmaj_off(row, k, K, 2)) = __float2bfloat16_rn(x);
+  } else if constexpr (KIND == KIND_TF32X3) {
     const float h = to_tf32(x);
     const float l = to_tf32(x - h);
     const uint32_t o = kmaj_off(row, k, K, 4);
@@ -182,6 +184,8 @@ __device__ __forceinline__ void put_split_f(unsigned char* base, uint32_t pstrid
 template <int KIND> struct Split;
 template <> struct Split<KIND_TF32X3> { static constexpr int parts = 2, esize = 4, kstep = 8; };
 template <> struct Split<KIND_BF16X3> { static constexpr int parts = 3, esize = 2, kstep = 16; };
+// a single BF16 product (no split): inference-grade, 8 significant bits per operand
+template <> struct Split<KIND_BF16X1> { static constexpr int parts = 1, esize = 2, kstep = 16; };
 
 // Issues D (+)= A B^T for one K chunk: A planes (M = 128 rows x K), B planes (N rows x K), K a
 // multiple of the MMA's K step.  Split products: TF32X3 {hh, hl, lh}; BF16X3 {00, 01, 10, 02, 11,
@@ -231,13 +235,13 @@ __device__ __forceinline__ void issue_kstep(uint32_t d_tmem, const unsigned char
   // products ordered from the smallest scale to the largest:
   //   TF32X3 (planes h = 0, l = 1): l*h, h*l, h*h
   //   BF16X3 (planes 0, 1, 2):      2*0, 1*1, 0*2, 1*0, 0*1, 0*0
-  constexpr int NP = KIND == KIND_TF32X3 ? 3 : 6;
+  constexpr int NP = KIND == KIND_TF32X3 ? 3 : (KIND == KIND_BF16X3 ? 6 : 1);
   constexpr int tf_a[3] = {1, 0, 0}, tf_b[3] = {0, 1, 0};
   constexpr int bf_a[6] = {2, 1, 0, 1, 0, 0}, bf_b[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
-    const int pa = KIND == KIND_TF32X3 ? tf_a[q] : bf_a[q];
-    const int pb = KIND == KIND_TF32X3 ? tf_b[q] : bf_b[q];
+    const int pa = KIND == KIND_TF32X3 ? tf_a[q] : (KIND == KIND_BF16X3 ? bf_a[q] : 0);
+    const int pb = KIND == KIND_TF32X3 ? tf_b[q] : (KIND == KIND_BF16X3 ? bf_b[q] : 0);
     const uint64_t da = sdesc(a0 + pa * a_plane, 128, sbo);
     const uint64_t db = sdesc(b0 + pb * b_plane, 128, sbo);
     if constexpr (KIND == KIND_TF32X3)

@@ -28,7 +28,8 @@ EXPORTS = [
     "ttns_occupations", "ttns_observables", "ttns_trajectory", "ttns_populations_device", "ttns_get_counters",
     "ttns_node_info", "ttns_get_node", "ttns_save", "ttns_load", "ttns_load_state", "ttns_last_error", "ttns_free",
     "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan", "ttns_selftest_wait_timeout",
-    "ttns_rho_from_root_noalloc", "ttns_autotune", "ttns_selftest_tc_gemm",
+    "ttns_rho_from_root_noalloc", "ttns_autotune", "ttns_selftest_tc_gemm", "ttns_mlp_gemm", "ttns_mlp_colsum",
+    "ttns_mlp_diff", "ttns_mlp_adam", "ttns_mlp_status",
 ]
 
 
@@ -108,6 +109,14 @@ def lib():
         L.ttns_plan.argtypes = [C.c_int, C.POINTER(ProblemC), C.POINTER(Options), C.POINTER(PlanInfo)]
         L.ttns_selftest_wait_timeout.argtypes = [C.c_longlong, C.POINTER(C.c_int)]
         L.ttns_selftest_tc_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, C.POINTER(C.c_int)]
+        vp = C.c_void_p
+        L.ttns_mlp_gemm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, C.c_int,
+                                    vp, C.c_int, C.c_int, vp, vp]
+        L.ttns_mlp_colsum.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp, vp]
+        L.ttns_mlp_diff.argtypes = [vp, vp, vp, C.c_longlong, C.c_float, vp]
+        L.ttns_mlp_adam.argtypes = [vp, vp, vp, vp, C.c_longlong, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int,
+                                    vp]
+        L.ttns_mlp_status.argtypes = [C.POINTER(C.c_int), C.c_int]
         L.ttns_rho_from_root_noalloc.argtypes = [C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]
         L.ttns_chain_ohmic.argtypes = [C.c_double, C.c_double, C.c_int, dp, dp, dp]
         L.ttns_chain_from_modes.argtypes = [C.c_int, dp, dp, C.c_int, dp, dp, dp]

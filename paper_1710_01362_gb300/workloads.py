@@ -218,3 +218,51 @@ def all_named():
         "sf_5state_4x20_d10_D20": sf_5state_4x20,
         "sf_er_5state_8x60_d20_D40": sf_er_5state_8x60,
     }
+
+
+# ---------------------------------------------------------------------------
+# Surrogate workload: the singlet-fission ER tree at reduced fidelity, parameterised by 30
+# numbers (the surrogate network's inputs)
+# ---------------------------------------------------------------------------
+
+SURROGATE_N_PARAMS = 30
+_SURROGATE_PATTERN_SEED = 777
+
+
+def surrogate_params(seed: int) -> np.ndarray:
+    """The 30 inputs: energies of LE+, LE-, CT+, CT- relative to TT (U[-0.2, 0.2] eV); the 10
+    electronic couplings (|V| in U[0.02, 0.10] eV, random sign, pairs in row order); per-chain
+    reorganisation energies (U[0.005, 0.08] eV, 8 chains); per-chain mean mode frequencies
+    (U[400, 1500] cm^-1, in eV)."""
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(-0.2, 0.2, size=4)
+    v = rng.uniform(0.02, 0.10, size=10) * np.where(rng.random(10) < 0.5, -1.0, 1.0)
+    lam = rng.uniform(0.005, 0.08, size=8)
+    wbar = rng.uniform(400.0, 1500.0, size=8) * CM1_TO_EV
+    return np.concatenate([e, v, lam, wbar])
+
+
+def surrogate_problem(x: np.ndarray, L: int = 8, d: int = 6, D: int = 8, dt: float = 1.0, n_steps: int = 200,
+                      n_modes: int = 12, name: str = "surrogate") -> Problem:
+    """The ER tree (5 states, 7 ER nodes, 8 chains of L sites) for one parameter vector.  The
+    coupling pattern of each chain is fixed (drawn once); chain i has n_modes modes at
+    wbar_i (0.5 + k / (n_modes - 1)), k = 0 .. n_modes - 1, with equal Huang-Rhys factors
+    whose reorganisation energy sum_k S_k w_k is lam_i."""
+    x = np.asarray(x, dtype=float)
+    n_el = 5
+    H_S = np.zeros((n_el, n_el), dtype=complex)
+    H_S[np.arange(4), np.arange(4)] = x[:4]
+    k = 4
+    for i in range(n_el):
+        for j in range(i + 1, n_el):
+            H_S[i, j] = H_S[j, i] = x[k]
+            k += 1
+    lam, wbar = x[14:22], x[22:30]
+    prng = np.random.default_rng(_SURROGATE_PATTERN_SEED)
+    envs = []
+    for i in range(8):
+        W = _pattern(prng, n_el, diagonal=(i < 4))
+        w = wbar[i] * (0.5 + np.arange(n_modes) / (n_modes - 1))
+        S = np.full(n_modes, lam[i] / w.sum())
+        envs.append(Environment(W_bar=W, spectral=("modes", w, w * np.sqrt(2.0 * S)), L=L, d=d, D=D))
+    return Problem(name=name, H_S=H_S, envs=envs, dt=dt, n_steps=n_steps, er_tree=True, D_er=D)
