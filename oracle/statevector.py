@@ -98,3 +98,55 @@ class Exact:
 
     def energy(self, psi: np.ndarray) -> float:
         return float(np.real(np.vdot(psi, self.H @ psi)))
+
+
+def dense_kinetic(problem):
+    """The chains' nuclear kinetic energy as a dense matrix, built term by term:
+    T = -(1/4) sum_m w_m (a^+ - a)_m^2 - (1/2) sum_m t_m (a^+ - a)_m (a^+ - a)_{m+1}
+    per chain (w_m onsite energies, t_m hoppings of the chain map)."""
+    n_el = problem.n_el
+    dims = [n_el]
+    for env in problem.envs:
+        dims += [env.d] * env.L
+    eye = [np.eye(d, dtype=complex) for d in dims]
+
+    def embed(ops):
+        mats = list(eye)
+        for pos, op in ops:
+            mats[pos] = op
+        return _kron_all(mats)
+
+    T = np.zeros((int(np.prod(dims)),) * 2, dtype=complex)
+    pos = 1
+    for env in problem.envs:
+        _, om, hop = chain_of(env.spectral, env.L)
+        d = env.d
+        a = np.diag(np.sqrt(np.arange(1, d, dtype=float)), 1).astype(complex)
+        P = a.conj().T - a
+        for n in range(env.L):
+            T = T - 0.25 * om[n] * embed([(pos + n, P @ P)])
+        for n in range(env.L - 1):
+            T = T - 0.5 * hop[n] * embed([(pos + n, P), (pos + n + 1, P)])
+        pos += env.L
+    return T
+
+
+def energy_surfaces(problem, H, T, psi, sigma_tol: float = 1e-7):
+    """Eq. 3-4 from a dense state: the Schmidt decomposition of psi for electronic | rest,
+    then <phi_i, j| H |phi_k, l> and the same with H - T, in the basis ordered bath-major.
+    Returns the ascending eigenvalues of H_eff and V_eff and the Schmidt values."""
+    n_el = problem.n_el
+    M = psi.reshape(n_el, -1)                       # electronic x rest
+    Uu, sv, Vh = np.linalg.svd(M, full_matrices=False)
+    keep = [k for k in range(len(sv)) if sv[k] > sigma_tol]
+    vecs = []
+    for k in keep:
+        phi = Vh[k]                                 # rest-space Schmidt vector
+        for l in range(n_el):
+            e = np.zeros(n_el, dtype=complex)
+            e[l] = 1.0
+            vecs.append(np.kron(e, phi))
+    B = np.array(vecs).T
+    Heff = B.conj().T @ H @ B
+    Veff = B.conj().T @ (H - T) @ B
+    return np.linalg.eigvalsh(Heff), np.linalg.eigvalsh(Veff), sv[keep]

@@ -41,7 +41,7 @@ from typing import Dict, List, Optional, Tuple
 import numpy as np
 
 from .linalg import expm_lanczos, householder_qr, KRYLOV_TOL, KRYLOV_MMAX
-from .model import Tree, build_tree, initial_tensors, lowering
+from .model import Coupling, Tree, build_tree, initial_tensors, lowering
 
 HBAR = 0.6582119569  # eV fs
 
@@ -299,6 +299,86 @@ class TTNS:
 
     def populations(self) -> np.ndarray:
         return np.real(np.diag(self.rho_el())).copy()
+
+    # ------------------------------------------------------------------ energy surfaces
+    def kinetic_tree(self) -> Tree:
+        """The tree with the nuclear kinetic energy T of the chains as its operator.
+
+        A chain is an orthogonal transform a_m = sum_n U_mn b_n of normal modes with
+        dimensionless momenta p_n = i (b_n^+ - b_n) / sqrt(2) and kinetic energy
+        w_n p_n^2 / 2, so T = (1/2) sum_mm' h_mm' P_m P_m' with h = U diag(w) U^T the chain's
+        tridiagonal matrix (onsite w_m, hoppings t_m) and P_m = i (a_m^+ - a_m) / sqrt(2):
+            T = -(1/4) sum_m w_m (a^+ - a)_m^2 - (1/2) sum_m t_m (a^+ - a)_m (a^+ - a)_{m+1},
+        with the operators truncated to the Fock states 0 .. d-1 (products of the truncated
+        matrices)."""
+        from .chain import chain_of
+        tr = self.tree
+        onsite = [None] * tr.n
+        coups = []
+        for i, env in enumerate(self.problem.envs):
+            _, om, hop = chain_of(env.spectral, env.L)
+            a = lowering(env.d)
+            P = a.conj().T - a
+            nodes = tr.chain_nodes[i]
+            for nn, v in enumerate(nodes):
+                onsite[v] = -0.25 * om[nn] * (P @ P)
+            for nn in range(env.L - 1):
+                coups.append(Coupling(nodes[nn], -0.5 * hop[nn] * P, nodes[nn + 1], P.copy()))
+        return Tree(parent=tr.parent, children=tr.children, phys=tr.phys, kind=tr.kind,
+                    site_index=tr.site_index, bond=tr.bond, onsite=onsite, couplings=coups, n_el=tr.n_el,
+                    chain_nodes=tr.chain_nodes, psi_el=tr.psi_el)
+
+    def _projected(self, op_tree: Tree):
+        """The root's local operator for op_tree (its environment blocks computed from the
+        current tensors, which are isometries toward the root after a step), as a
+        function on root-shaped tensors."""
+        other = object.__new__(TTNS)
+        other.__dict__.update(self.__dict__)
+        other.tree = op_tree
+        other.env = {}
+        other._init_envs()
+        return lambda x: other.heff(0, x)
+
+    def energy_surfaces(self, sigma_tol: float = 1e-7):
+        """Energy surfaces of Eq. 3-4 at the current time (the centre at the root).
+
+        The bath states phi_k are the environment Schmidt vectors of the state for the
+        bipartition electronic | everything else (the SVD of the root tensor matricised as
+        other legs x electronic leg), kept where the Schmidt value exceeds sigma_tol.  With
+        the basis |k, l> = |phi_k> |l> (bath-major),
+            H_eff[(i j), (k l)] = <phi_i| <j| H |phi_k> |l>,   V_eff = H_eff - T_eff,
+        T the chains' nuclear kinetic energy (kinetic_tree).  Returns the ascending
+        eigenvalues of H_eff (total energy surfaces) and of V_eff (potential energy
+        surfaces), the Schmidt values, and both matrices."""
+        tr = self.tree
+        A = self.A[0]
+        n_el = tr.n_el
+        M = A.reshape(-1, n_el)                       # (other legs) x electronic
+        rho = M.T @ M.conj()                          # rho[s, s'] = sum_r M[r, s] conj(M[r, s'])
+        w, U = np.linalg.eigh(rho)
+        order = np.argsort(w)[::-1]
+        w, U = w[order], U[:, order]
+        sig = np.sqrt(np.clip(w, 0.0, None))
+        keep = [k for k in range(n_el) if sig[k] > sigma_tol]
+        phis = [(M @ U[:, k].conj()) / sig[k] for k in keep]
+        basis = []
+        for ph in phis:
+            for l in range(n_el):
+                X = np.zeros_like(M)
+                X[:, l] = ph
+                basis.append(X.reshape(A.shape))
+        H = self._projected(tr)
+        T = self._projected(self.kinetic_tree())
+        nb = len(basis)
+        Heff = np.zeros((nb, nb), dtype=complex)
+        Teff = np.zeros((nb, nb), dtype=complex)
+        for c, X in enumerate(basis):
+            hx, tx = H(X), T(X)
+            for r, Y in enumerate(basis):
+                Heff[r, c] = np.vdot(Y, hx)
+                Teff[r, c] = np.vdot(Y, tx)
+        Veff = Heff - Teff
+        return np.linalg.eigvalsh(Heff), np.linalg.eigvalsh(Veff), sig[keep], Heff, Veff
 
     # ------------------------------------------------------------------ dense state
     def to_dense(self) -> np.ndarray:
