@@ -195,6 +195,28 @@ ttns_status ttns_occupations(ttns_tree* tree, int tree_idx, double* occ_out);
 /* norm and energy <H> (eV, with the shifted H_S) of tree tree_idx. */
 ttns_status ttns_observables(ttns_tree* tree, int tree_idx, double* norm, double* energy);
 
+/* Energy surfaces (Eq. 3-4, Results, "Dynamic energy surfaces") of tree tree_idx at the
+ * current time.  The bath states |phi_k> are the environment Schmidt vectors of the state for
+ * the bipartition electronic | environment (from the root tensor, the orthogonality centre),
+ * kept where the Schmidt value exceeds sigma_tol; in the basis |phi_k>|l> (bath-major)
+ *   H_eff[(i j), (k l)] = <phi_i, j| H |phi_k, l>,   V_eff = H_eff - T_eff,
+ * with T the chains' nuclear kinetic energy,
+ *   T = -(1/4) sum_m w_m (a^+ - a)_m^2 - (1/2) sum_m t_m (a^+ - a)_m (a^+ - a)_{m+1}
+ * (the normal modes' sum w_n p_n^2 / 2 in the chain basis).  Outputs (caller-owned host
+ * buffers): tes and pes, n_bath * n_el ascending eigenvalues of H_eff (total energy surfaces)
+ * and V_eff (potential energy surfaces); sigma, the n_el Schmidt values (descending);
+ * *n_bath.  Needs n_el <= 16 and n_bath * n_el <= 32 (TTNS_E_INVALID otherwise).  Runs the
+ * kinetic energy's environment pass and small FP64 kernels; synchronises the stream. */
+ttns_status ttns_energy_surfaces(ttns_tree* tree, int tree_idx, double sigma_tol, double* tes, double* pes,
+                                 double* sigma, int* n_bath);
+
+/* Entanglement entropies of tree tree_idx at the current time: S_out[0] is the von Neumann
+ * entropy -sum lambda ln lambda of the electronic reduced density matrix (system vs.
+ * environment), S_out[v] (v = 1 .. n_nodes - 1) that of the bond between node v and its parent
+ * (the eigenvalues of the bond's density matrix from the downward pass from the root).
+ * Node numbering as in ttns_node_info.  S_out holds n_nodes doubles (caller-owned). */
+ttns_status ttns_bond_entropies(ttns_tree* tree, int tree_idx, double* S_out);
+
 /* Copies the recorded rho_S trajectory of tree tree_idx: out holds
  * max_steps*n_el*n_el complex; *n_written receives the number of steps copied. */
 ttns_status ttns_trajectory(ttns_tree* tree, int tree_idx, double* out, int max_steps, int* n_written);

@@ -58,6 +58,7 @@ class TTNS:
         self.A: List[np.ndarray] = initial_tensors(self.tree)
         self.tol = tol
         self.mmax = mmax
+        self.qr_cutoff = getattr(problem, "qr_cutoff", None)
         self.stats: Dict[str, int] = {}
         self.t = 0.0
         t = self.tree
@@ -194,7 +195,7 @@ class TTNS:
         l = tr.leg_of(v, u)
         Am = np.moveaxis(A, l, -1)
         shp = Am.shape
-        Q, R = householder_qr(Am.reshape(-1, shp[-1]))
+        Q, R = householder_qr(Am.reshape(-1, shp[-1]), self.qr_cutoff)
         self.A[v] = np.moveaxis(Q.reshape(shp), -1, l)
         return R
 
@@ -285,6 +286,43 @@ class TTNS:
                 others = [k for k in range(Q.ndim) if k != l]
                 stack.append((c, np.tensordot(X, Q.conj(), axes=(others, others))))
         return out
+
+    def bond_densities(self) -> Dict[int, np.ndarray]:
+        """Density matrix of every non-root node's parent bond, by the downward pass from the
+        root (the centre): rho_in(v)[b, b'] in the bond basis of v's tensor."""
+        tr = self.tree
+        out = {}
+        A = self.A[0]
+        stack = []
+        for c in tr.children[0]:
+            l = tr.leg_of(0, c)
+            others = [k for k in range(A.ndim) if k != l]
+            stack.append((c, np.tensordot(A, A.conj(), axes=(others, others))))
+        while stack:
+            v, rho_in = stack.pop()
+            out[v] = rho_in
+            Q = self.A[v]
+            X = apply_factor(Q, 0, rho_in.T)
+            for c in tr.children[v]:
+                l = tr.leg_of(v, c)
+                others = [k for k in range(Q.ndim) if k != l]
+                stack.append((c, np.tensordot(X, Q.conj(), axes=(others, others))))
+        return out
+
+    def bond_entropies(self) -> np.ndarray:
+        """[S(rho_S), S(bond of node 1), ...]: von Neumann entropies -sum l ln l of the
+        electronic reduced density matrix and of every bond's density matrix (Results, the
+        entanglement entropy that guides the tree's design)."""
+        def ent(rho):
+            w = np.linalg.eigvalsh(0.5 * (rho + rho.conj().T))
+            w = w[w > 1e-300]
+            return float(-np.sum(w * np.log(w)))
+        dens = self.bond_densities()
+        S = np.zeros(self.tree.n)
+        S[0] = ent(self.rho_el())
+        for v, rho in dens.items():
+            S[v] = ent(rho)
+        return S
 
     def occupations(self) -> np.ndarray:
         """<a^+ a> of every chain site, chains in order, sites in chain order."""

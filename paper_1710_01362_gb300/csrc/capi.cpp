@@ -22,6 +22,16 @@ cudaError_t launch_energy(const KernelParams& P, int node, int terms, int n2, do
                           double* out, cudaStream_t st);
 cudaError_t launch_occ(const double2* dens, int d, double* out, cudaStream_t st);
 cudaError_t launch_wait_selftest(Ctl* ctl, long long spin_limit, int skip, cudaStream_t st);
+cudaError_t launch_apply_x(const KernelParams& P, int node, int terms, int n2, const double2* x, double2* y,
+                           int nblocks, cudaStream_t st);
+cudaError_t launch_herm_jacobi(const double2* base, const long long* offs, const int* ns, const int* lds, int count,
+                               int n_max, double* evals, double2* evecs, cudaStream_t st);
+cudaError_t launch_bath_states(const double2* A, long long R, int n_el, const double2* U, const double* sig, int nb,
+                               double2* Phi, cudaStream_t st);
+cudaError_t launch_build_x(const double2* Phi, int k, int l, long long R, int n_el, double2* X, cudaStream_t st);
+cudaError_t launch_project(const double2* y, const double2* Phi, long long R, int n_el, int nb, double* partials,
+                           int nblocks, double* out, cudaStream_t st);
+cudaError_t launch_sub(const double* a, const double* b, double* c, int n, cudaStream_t st);
 }  // namespace ttns
 
 using namespace ttns;
@@ -70,6 +80,9 @@ struct ttns_tree {
   // was repeated as a plain cluster launch (see run_launch)
   std::vector<std::pair<double, int>> pending;
   long long launch_fallbacks = 0;
+  // scratch of the energy surfaces and bond entropies (allocated on first use)
+  double* surf = nullptr;
+  long long surf_size = 0;
 };
 
 // Launch of the persistent kernel with the tree set's launch options.  launch_flags bit 1 is a
@@ -389,7 +402,8 @@ static ttns_status device_init(ttns_tree* t) {
   t->o_bond = 1024LL * d2;
   t->o_site = t->o_bond + nn * d2;
   t->o_occ = t->o_site + nn * d2;
-  t->o_rho = t->o_occ + nn + 64;
+  // rho_S is read as complex (16-byte loads) by the eigen kernels: 256-byte aligned
+  t->o_rho = (t->o_occ + nn + 64 + 31) & ~31LL;
   t->o_en = t->o_rho + 2 * 64 * 64;
   t->obs_size = t->o_en + 16;
   if ((s = dalloc(t, &t->obs, t->obs_size)) != TTNS_OK) return s;
@@ -661,11 +675,25 @@ extern "C" ttns_status ttns_reduced_density_matrix(ttns_tree* t, int tree_idx, d
   return TTNS_OK;
 }
 
+// Downward pass of bond densities from the root (the centre): the parent-bond density of
+// every non-root node v at obs + o_bond + v * 2 maxD^2 (D_v x D_v, row-major); with sites,
+// also every chain site's local density and <n> (occupations).
+static ttns_status downward_pass(ttns_tree* t, int tree_idx, bool sites);
+
 extern "C" ttns_status ttns_occupations(ttns_tree* t, int tree_idx, double* occ_out) {
   if (!t || !occ_out) return fail(TTNS_E_INVALID, "NULL argument");
   if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
   ttns_status s = ttns_sync(t);
   if (s != TTNS_OK) return s;
+  if ((s = downward_pass(t, tree_idx, true)) != TTNS_OK) return s;
+  const TreeDesc& td = t->C.trees[tree_idx];
+  CUDA_TRY(cudaMemcpyAsync(occ_out, t->obs + t->o_occ, sizeof(double) * td.n_sites, cudaMemcpyDeviceToHost, t->stream));
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  return TTNS_OK;
+}
+
+static ttns_status downward_pass(ttns_tree* t, int tree_idx, bool sites) {
+  ttns_status s;
   const HostTree& h = t->C.host[tree_idx];
   const TreeDesc& td = t->C.trees[tree_idx];
   const int maxD = t->C.max_D;
@@ -694,14 +722,183 @@ extern "C" ttns_status ttns_occupations(ttns_tree* t, int tree_idx, double* occ_
     for (int c : h.children[v]) {
       if ((s = density(t, gv, h.leg_of(v, c), rin, dens + (long long)c * 2 * maxD * maxD)) != TTNS_OK) return s;
     }
-    if (h.parent[v] >= 0 && h.phys[v] > 0 && site_pos[v] >= 0) {
+    if (sites && h.parent[v] >= 0 && h.phys[v] > 0 && site_pos[v] >= 0) {
       double* sd = site_dens + (long long)site_pos[v] * 2 * maxD * maxD;
       if ((s = density(t, gv, h.phys_leg(v), rin, sd)) != TTNS_OK) return s;
       CUDA_TRY(launch_occ((const double2*)sd, h.phys[v], occ_dev + site_pos[v], t->stream));
     }
   }
-  CUDA_TRY(cudaMemcpyAsync(occ_out, occ_dev, sizeof(double) * td.n_sites, cudaMemcpyDeviceToHost, t->stream));
+  return TTNS_OK;
+}
+
+static ttns_status surface_scratch(ttns_tree* t, long long doubles) {
+  if (t->surf_size >= doubles) return TTNS_OK;
+  ttns_status s = dalloc(t, &t->surf, (size_t)doubles);
+  if (s != TTNS_OK) return s;
+  t->surf_size = doubles;
+  return TTNS_OK;
+}
+
+// Batched Hermitian eigenvalues (and optionally vectors) of count matrices in device memory.
+static ttns_status eig_batch(ttns_tree* t, const double2* base, const std::vector<long long>& offs,
+                             const std::vector<int>& ns, double* d_evals, double2* d_evecs, long long* d_offs,
+                             int* d_ns) {
+  const int count = (int)offs.size();
+  int n_max = 1;
+  for (int n : ns) n_max = std::max(n_max, n);
+  if (n_max > 64) return fail(TTNS_E_INVALID, "eigenproblem larger than 64");
+  CUDA_TRY(cudaMemcpyAsync(d_offs, offs.data(), sizeof(long long) * count, cudaMemcpyHostToDevice, t->stream));
+  CUDA_TRY(cudaMemcpyAsync(d_ns, ns.data(), sizeof(int) * count, cudaMemcpyHostToDevice, t->stream));
+  CUDA_TRY(cudaMemcpyAsync(d_ns + count, ns.data(), sizeof(int) * count, cudaMemcpyHostToDevice, t->stream));
+  CUDA_TRY(launch_herm_jacobi(base, d_offs, d_ns, d_ns + count, count, n_max, d_evals, d_evecs, t->stream));
+  return TTNS_OK;
+}
+
+// The environment pass of the chains' kinetic energy (persistent kernel, phase 2), repeated as
+// a plain cluster launch if the launch check refused it.
+static ttns_status kinetic_envs(ttns_tree* t) {
+  KernelParams P2 = t->P;
+  P2.dt = 0.0;
+  P2.n_steps = 1;
+  CUDA_TRY(launch_sweep(P2, 2, t->grid, t->cluster, !(t->opt.launch_flags & 1), t->stream));
   CUDA_TRY(cudaStreamSynchronize(t->stream));
+  Ctl h;
+  CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  if (launch_refused(h) && !(t->opt.launch_flags & 1)) {
+    t->opt.launch_flags |= 1;
+    ++t->launch_fallbacks;
+    h.status = h.err_where = h.err_node = 0;
+    CUDA_TRY(cudaMemcpy(t->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
+    CUDA_TRY(launch_sweep(P2, 2, t->grid, t->cluster, 0, t->stream));
+    CUDA_TRY(cudaStreamSynchronize(t->stream));
+    CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  }
+  if (h.status != 0) return fail((ttns_status)h.status, std::string("kinetic environment pass: ") + status_text(h));
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_energy_surfaces(ttns_tree* t, int tree_idx, double sigma_tol, double* tes, double* pes,
+                                            double* sigma, int* n_bath) {
+  if (!t || !tes || !pes || !sigma || !n_bath) return fail(TTNS_E_INVALID, "NULL argument");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  if (!(sigma_tol >= 0.0)) return fail(TTNS_E_INVALID, "sigma_tol must be >= 0");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  const TreeDesc& td = t->C.trees[tree_idx];
+  const int ne = td.n_el;
+  if (ne > 16) return fail(TTNS_E_INVALID, "energy surfaces need n_el <= 16");
+  const NodeDesc& rootd = t->C.nodes[td.node0];
+  const long long R = rootd.size / ne;
+  // scratch: evals (2 x 64), evecs (64 x 64 complex), U and sigma of the kept states, H / T / V
+  // (32 x 32 complex each), projection partials (256 blocks x 2 x 32), offsets and sizes
+  const long long o_ev = 0, o_vec = 128, o_u = o_vec + 2 * 64 * 64, o_sig = o_u + 2 * 16 * 16,
+                  o_h = o_sig + 64, o_t = o_h + 2 * 32 * 32, o_v = o_t + 2 * 32 * 32, o_part = o_v + 2 * 32 * 32,
+                  o_offs = o_part + 256 * 2 * 32, o_ns = o_offs + 8, total = o_ns + 8;
+  if ((s = surface_scratch(t, total)) != TTNS_OK) return s;
+  double* sc = t->surf;
+  // 1. environment blocks of the kinetic energy at the current state
+  if ((s = kinetic_envs(t)) != TTNS_OK) return s;
+  // 2. Schmidt decomposition through rho_S = A^T conj(A): eigenvectors and values
+  double* rho = t->obs + t->o_rho;
+  if ((s = density(t, td.node0, td.root_phys_leg, nullptr, rho)) != TTNS_OK) return s;
+  if ((s = eig_batch(t, (const double2*)rho, {0}, {ne}, sc + o_ev, (double2*)(sc + o_vec), (long long*)(sc + o_offs),
+                     (int*)(sc + o_ns))) != TTNS_OK)
+    return s;
+  std::vector<double> ev(64);
+  std::vector<double2> vec(64 * 64);
+  CUDA_TRY(cudaMemcpyAsync(ev.data(), sc + o_ev, sizeof(double) * 64, cudaMemcpyDeviceToHost, t->stream));
+  CUDA_TRY(cudaMemcpyAsync(vec.data(), sc + o_vec, sizeof(double2) * 64 * 64, cudaMemcpyDeviceToHost, t->stream));
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  std::vector<int> keep;
+  for (int k = ne - 1; k >= 0; --k) {
+    const double sg = std::sqrt(std::max(ev[k], 0.0));
+    sigma[ne - 1 - k] = sg;
+    if (sg > sigma_tol) keep.push_back(k);
+  }
+  const int nb = (int)keep.size();
+  const int nv = nb * ne;
+  if (nv > 32) return fail(TTNS_E_INVALID, "energy surfaces need (bath states) x n_el <= 32");
+  *n_bath = nb;
+  if (nb == 0) return fail(TTNS_E_INVALID, "no Schmidt value above sigma_tol");
+  std::vector<double2> U(ne * nb);
+  std::vector<double> sg(nb);
+  for (int k = 0; k < nb; ++k) {
+    sg[k] = std::sqrt(std::max(ev[keep[k]], 0.0));
+    for (int q = 0; q < ne; ++q) U[q * nb + k] = vec[q * 64 + keep[k]];
+  }
+  CUDA_TRY(cudaMemcpyAsync(sc + o_u, U.data(), sizeof(double2) * U.size(), cudaMemcpyHostToDevice, t->stream));
+  CUDA_TRY(cudaMemcpyAsync(sc + o_sig, sg.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, t->stream));
+  // 3. bath states and the projected H_eff(root), T_eff(root) in the basis |phi_k, l>
+  const long long kv = t->P.kvec;
+  double2* slot = t->work + (long long)(t->P.mmax + t->P.n_tmp + 2) * kv;
+  double2 *Phi = slot, *X = slot + kv, *Y = slot + 2 * kv;
+  const double2* A = t->pool + rootd.off;
+  CUDA_TRY(launch_bath_states(A, R, ne, (const double2*)(sc + o_u), sc + o_sig, nb, Phi, t->stream));
+  const int nbl = (int)std::min<long long>(1024, (rootd.size + 255) / 256);
+  const int npb = (int)std::min<long long>(256, R / 64 + 1);
+  const int n2h = t->C.lists[td.heff_terms].n2, n2t = t->C.lists[td.teff_terms].n2;
+  for (int c = 0; c < nv; ++c) {
+    CUDA_TRY(launch_build_x(Phi, c / ne, c % ne, R, ne, X, t->stream));
+    CUDA_TRY(launch_apply_x(t->P, td.node0, td.heff_terms, n2h, X, Y, nbl, t->stream));
+    CUDA_TRY(launch_project(Y, Phi, R, ne, nb, sc + o_part, npb, sc + o_h + 2LL * c * nv, t->stream));
+    CUDA_TRY(launch_apply_x(t->P, td.node0, td.teff_terms, n2t, X, Y, nbl, t->stream));
+    CUDA_TRY(launch_project(Y, Phi, R, ne, nb, sc + o_part, npb, sc + o_t + 2LL * c * nv, t->stream));
+  }
+  // 4. V = H - T and the eigenvalues of both (the matrices are stored by columns: their
+  //    transposes, conj(H) and conj(V), have the same eigenvalues)
+  CUDA_TRY(launch_sub(sc + o_h, sc + o_t, sc + o_v, 2 * nv * nv, t->stream));
+  if ((s = eig_batch(t, (const double2*)sc, {o_h / 2, o_v / 2}, {nv, nv}, sc + o_ev, nullptr,
+                     (long long*)(sc + o_offs), (int*)(sc + o_ns))) != TTNS_OK)
+    return s;
+  std::vector<double> ev2(128);
+  CUDA_TRY(cudaMemcpyAsync(ev2.data(), sc + o_ev, sizeof(double) * 128, cudaMemcpyDeviceToHost, t->stream));
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  for (int k = 0; k < nv; ++k) {
+    tes[k] = ev2[k];
+    pes[k] = ev2[64 + k];
+  }
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_bond_entropies(ttns_tree* t, int tree_idx, double* S_out) {
+  if (!t || !S_out) return fail(TTNS_E_INVALID, "NULL argument");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  const TreeDesc& td = t->C.trees[tree_idx];
+  const HostTree& h = t->C.host[tree_idx];
+  const int n = h.n();
+  const int maxD = t->C.max_D;
+  if ((s = downward_pass(t, tree_idx, false)) != TTNS_OK) return s;
+  double* rho = t->obs + t->o_rho;
+  if ((s = density(t, td.node0, td.root_phys_leg, nullptr, rho)) != TTNS_OK) return s;
+  // matrices: rho_S (root), then every node's parent-bond density
+  const long long o_ev = 0, o_offs = 64LL * n, o_ns = o_offs + n + 8, total = o_ns + n + 8;
+  if ((s = surface_scratch(t, std::max<long long>(total, 1))) != TTNS_OK) return s;
+  // rho_S and the bond densities live in one buffer (obs): offsets relative to obs as double2
+  std::vector<long long> offs(n);
+  std::vector<int> ns(n);
+  offs[0] = (t->o_rho) / 2;
+  ns[0] = td.n_el;
+  for (int v = 1; v < n; ++v) {
+    offs[v] = (t->o_bond + (long long)v * 2 * maxD * maxD) / 2;
+    ns[v] = h.bond[v];
+  }
+  double* sc = t->surf;
+  if ((s = eig_batch(t, (const double2*)t->obs, offs, ns, sc + o_ev, nullptr, (long long*)(sc + o_offs),
+                     (int*)(sc + o_ns))) != TTNS_OK)
+    return s;
+  std::vector<double> ev(64LL * n);
+  CUDA_TRY(cudaMemcpyAsync(ev.data(), sc + o_ev, sizeof(double) * 64 * n, cudaMemcpyDeviceToHost, t->stream));
+  CUDA_TRY(cudaStreamSynchronize(t->stream));
+  for (int v = 0; v < n; ++v) {
+    double S = 0.0;
+    for (int a = 0; a < ns[v]; ++a) {
+      const double l = ev[(long long)v * 64 + a];
+      if (l > 1e-300) S -= l * std::log(l);
+    }
+    S_out[v] = S;
+  }
   return TTNS_OK;
 }
 

@@ -100,6 +100,10 @@ struct TreeDesc {
   long long traj_off; // trajectory buffer offset (complex), n_el^2 per step
   int max_node;       // largest tensor (complex elements)
   int n_sites;        // chain sites (occupation outputs)
+  int obs_first;      // environment pass of the chains' kinetic-energy operator (energy surfaces)
+  int obs_count;
+  int heff_terms;     // term list of H_eff(root) and of T_eff(root)
+  int teff_terms;
 };
 
 // Device-side control block (status word, barrier, counters).

@@ -226,6 +226,39 @@ HostTree build_host_tree(const TreeInput& in) {
   return t;
 }
 
+HostTree kinetic_tree(const HostTree& h, const TreeInput& in) {
+  HostTree k = h;
+  k.onsite.assign(h.n(), {});
+  k.coups.clear();
+  for (int i = 0; i < in.n_env; ++i) {
+    const int d = in.d[i];
+    // P = a^+ - a and P^2 (products of the truncated matrices)
+    std::vector<cplx> P(d * d, 0.0), P2(d * d, 0.0);
+    for (int s = 1; s < d; ++s) {
+      P[s * d + (s - 1)] = std::sqrt((double)s);
+      P[(s - 1) * d + s] = -std::sqrt((double)s);
+    }
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) {
+        cplx acc = 0.0;
+        for (int q = 0; q < d; ++q) acc += P[r * d + q] * P[q * d + c];
+        P2[r * d + c] = acc;
+      }
+    const auto& nodes = h.chain_nodes[i];
+    for (int s = 0; s < in.L[i]; ++s) {
+      std::vector<cplx> on(d * d);
+      for (int q = 0; q < d * d; ++q) on[q] = -0.25 * in.omega[i][s] * P2[q];
+      k.onsite[nodes[s]] = on;
+    }
+    for (int s = 0; s + 1 < in.L[i]; ++s) {
+      std::vector<cplx> pa(d * d);
+      for (int q = 0; q < d * d; ++q) pa[q] = -0.5 * in.hop[i][s] * P[q];
+      k.coups.push_back({nodes[s], pa, nodes[s + 1], P});
+    }
+  }
+  return k;
+}
+
 // ---------------------------------------------------------------------------
 // compilation
 // ---------------------------------------------------------------------------
@@ -413,6 +446,65 @@ struct TreeCompiler {
   int team_for(int size, bool qr = false) const {
     if (batched) return TEAM_CLUSTER;
     return size >= (qr ? qr_grid_threshold : grid_threshold) ? TEAM_GRID : TEAM_CLUSTER;
+  }
+
+  // Environment pass of a second operator on the tree of an already compiled tree (its
+  // nodes node0_existing ..): environment blocks toward the root only, the operator's
+  // constant matrices, one instruction per edge in post-order, and the root's term list.
+  // Returns (first instruction, count, root term list).
+  std::vector<long long> op_reg_off, op_reg_len;
+  void compile_operator(int node0_existing, int* first, int* count, int* root_terms) {
+    const int n = t.n();
+    sub.assign(n, std::vector<char>(n, 0));
+    for (int v = n - 1; v >= 0; --v) {
+      sub[v][v] = 1;
+      for (int c : t.children[v])
+        for (int x = 0; x < n; ++x)
+          if (sub[c][x]) sub[v][x] = 1;
+    }
+    node0 = node0_existing;
+    onsite_off.assign(n, -1);
+    opa_off.assign(t.coups.size(), -1);
+    opb_off.assign(t.coups.size(), -1);
+    op_reg_off.assign(n, 0);
+    op_reg_len.assign(n, 0);
+    for (int v = 0; v < n; ++v) {
+      const long long reg0 = (long long)C.pool_init.size();
+      for (int w : t.children[v]) {
+        EnvInfo E;
+        E.D = t.bond[w];
+        for (int k = 0; k < (int)t.coups.size(); ++k) {
+          bool a = in_piece(w, v, t.coups[k].va), b = in_piece(w, v, t.coups[k].vb);
+          if (a != b) E.chans.push_back(k);
+        }
+        E.off = push_zeros((long long)(1 + E.chans.size()) * E.D * E.D);
+        env[{w, v}] = E;
+      }
+      if (!t.onsite[v].empty()) onsite_off[v] = push_operator(t.onsite[v]);
+      for (int k = 0; k < (int)t.coups.size(); ++k) {
+        if (t.coups[k].va == v) opa_off[k] = push_operator(t.coups[k].opa);
+        if (t.coups[k].vb == v) opb_off[k] = push_operator(t.coups[k].opb);
+      }
+      finish_sparse();
+      op_reg_off[v] = reg0;
+      op_reg_len[v] = (long long)C.pool_init.size() - reg0;
+    }
+    std::vector<int> post;
+    std::function<void(int)> rec = [&](int v) {
+      for (int c : t.children[v]) rec(c);
+      post.push_back(v);
+    };
+    rec(0);
+    *first = (int)C.prog.size();
+    for (int v : post)
+      if (t.parent[v] >= 0) {
+        emit_env(v, t.parent[v]);
+        Instr& I = C.prog.back();
+        I.rega_off = op_reg_off[v];
+        I.rega_len = (int)op_reg_len[v];
+      }
+    *count = (int)C.prog.size() - *first;
+    *root_terms = node_terms(0, -1);
   }
 
   void compile() {
@@ -694,6 +786,13 @@ Compiled compile_trees(const std::vector<TreeInput>& inputs, bool batched, int g
   for (size_t i = 0; i < inputs.size(); ++i) {
     TreeCompiler tc(C.host[i], C, (int)i, batched, grid_threshold, qr_grid_threshold);
     tc.compile();
+    TreeDesc& td = C.trees.back();
+    td.heff_terms = tc.heff_list.at(0);
+    // the chains' kinetic energy on the same tree (energy surfaces): its environment pass
+    // reads the node tensors of this tree
+    const HostTree kin = kinetic_tree(C.host[i], inputs[i]);
+    TreeCompiler kc(kin, C, (int)i, batched, grid_threshold, qr_grid_threshold);
+    kc.compile_operator(td.node0, &td.obs_first, &td.obs_count, &td.teff_terms);
   }
   // trajectory buffers at the end of the pool
   for (auto& td : C.trees) {

@@ -55,6 +55,12 @@ struct TreeInput {
 
 HostTree build_host_tree(const TreeInput& in);
 
+// The same tree with the chains' nuclear kinetic energy as its operator:
+//   T = -(1/4) sum_m w_m (a^+ - a)_m^2 - (1/2) sum_m t_m (a^+ - a)_m (a^+ - a)_{m+1}
+// per chain (w_m onsite energies, t_m hoppings of the chain map): the kinetic energy of the
+// normal modes, sum_n w_n p_n^2 / 2, written in the chain basis.
+HostTree kinetic_tree(const HostTree& h, const TreeInput& in);
+
 // Flattened device tables for a set of trees.
 struct Compiled {
   std::vector<NodeDesc> nodes;

@@ -1934,7 +1934,8 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     team_reduce_vec(tm, mine, redo, 4 * n + 1);
   }
   pc.lap(P.ctl, 8);
-  const double thr = P.qr_cutoff * sqrt(redo[4 * n]);
+  const double fro_m = sqrt(redo[4 * n]);  // ||M||_F (redo is reused by the column loop)
+  const double thr = P.qr_cutoff * fro_m;
   for (int j = 0; j < n; ++j) {
     // reflector of column j: alpha = -phase(x0) sigma, vh = x0 - alpha = x0 (1 + sigma / |x0|),
     // |vh| = |x0| + sigma, |v|^2 = d_j + |vh|^2, tau = 2 / |v|^2.  Written so that the FP64
@@ -2116,15 +2117,31 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     qs.ph[j] = aa > 0.0 ? make_double2(a.x / aa, a.y / aa) : make_double2(1.0, 0.0);
   }
   __syncthreads();
-  // R (row j scaled by conj(ph_j)) into the bond buffer: R[j][k] = W[k][j] (k > j), diag alpha_j
+  // R (row j scaled by conj(ph_j)) into the bond buffer: R[j][k] = W[k][j] (k > j), diag alpha_j,
+  // rescaled to ||R||_F = ||M||_F (the weight of dropped sub-columns returns to the kept content)
   if (tm.rank == 0) {
+    __shared__ double s_rn[NWARP];
+    double loc = 0.0;
+    for (int idx = threadIdx.x; idx < n * n; idx += NT) {
+      const int j = idx / n, k = idx % n;
+      double2 r = make_double2(0, 0);
+      if (k > j) r = W[(long long)k * rows + j];
+      else if (k == j) r = qs.rdiag[j];
+      loc = fma(r.x, r.x, fma(r.y, r.y, loc));
+    }
+    loc = warp_sum(loc);
+    if (lane == 0) s_rn[warp] = loc;
+    __syncthreads();
+    double rn = 0.0;
+    for (int w = 0; w < NWARP; ++w) rn += s_rn[w];
+    const double scale = rn > 0.0 ? fro_m / sqrt(rn) : 1.0;
     for (int idx = threadIdx.x; idx < n * n; idx += NT) {
       const int j = idx / n, k = idx % n;
       double2 r = make_double2(0, 0);
       if (k > j) r = W[(long long)k * rows + j];
       else if (k == j) r = qs.rdiag[j];
       const double2 p = qs.ph[j];
-      Rout[idx] = make_double2(r.x * p.x + r.y * p.y, r.y * p.x - r.x * p.y);
+      Rout[idx] = make_double2(scale * (r.x * p.x + r.y * p.y), scale * (r.y * p.x - r.x * p.y));
     }
   }
   // Q[r][c] = (delta_rc - sum_j V[r][j] Z[j][c]) * ph_c over the own rows, one (c, r) pair
@@ -2343,9 +2360,9 @@ __device__ void run(const KernelParams& P, int phase) {
   if (P.batched) {
     for (int tree = cluster_id; tree < P.n_trees; tree += n_clusters) {
       const TreeDesc& td = P.trees[tree];
-      const int first = phase == 0 ? td.init_first : td.prog_first;
-      const int count = phase == 0 ? td.init_count : td.prog_count;
-      const int nst = phase == 0 ? 1 : P.n_steps;
+      const int first = phase == 0 ? td.init_first : (phase == 2 ? td.obs_first : td.prog_first);
+      const int count = phase == 0 ? td.init_count : (phase == 2 ? td.obs_count : td.prog_count);
+      const int nst = phase == 1 ? P.n_steps : 1;
       for (int s = 0; s < nst; ++s) {
         for (int k = 0; k < count; ++k) {
           exec<T>(P, ct, P.prog[first + k], cwork);
@@ -2364,9 +2381,9 @@ __device__ void run(const KernelParams& P, int phase) {
   gt.ctl = P.ctl;
   gt.spin_limit = P.spin_limit;
   const TreeDesc& td = P.trees[0];
-  const int first = phase == 0 ? td.init_first : td.prog_first;
-  const int count = phase == 0 ? td.init_count : td.prog_count;
-  const int nst = phase == 0 ? 1 : P.n_steps;
+  const int first = phase == 0 ? td.init_first : (phase == 2 ? td.obs_first : td.prog_first);
+  const int count = phase == 0 ? td.init_count : (phase == 2 ? td.obs_count : td.prog_count);
+  const int nst = phase == 1 ? P.n_steps : 1;
   int prev = TEAM_GRID;
   for (int s = 0; s < nst; ++s) {
     for (int k = 0; k < count; ++k) {
@@ -2549,6 +2566,48 @@ __global__ void k_stage1(KernelParams P, int node, int terms) {
       tmp[t * P.kvec + idx] = a;
     }
   }
+}
+
+// H x for an explicit input x with a node's term list (FP64): stage 1 of the two-stage terms
+// into the worker-0 temporaries, then y = the sum of all terms
+__global__ void k_stage1_x(KernelParams P, int node, int terms, const double2* x) {
+  const NodeDesc nd = P.nodes[node];
+  const TermList L = P.lists[terms];
+  const Term* tl = P.terms + L.first + (L.count - L.n2);
+  double2* tmp = P.work + (long long)P.mmax * P.kvec;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nd.size;
+       idx += (long long)gridDim.x * blockDim.x) {
+    for (int t = 0; t < L.n2; ++t) {
+      const Factor f = tl[t].f[0];
+      LegPos lp = leg_pos(nd, f.leg, idx);
+      tmp[t * P.kvec + idx] = mode_dot<double>(P.pool + f.mat + (long long)lp.i * nd.dims[f.leg], nd.dims[f.leg], x,
+                                               lp.base, nd.strides[f.leg]);
+    }
+  }
+}
+
+__global__ void k_apply_x(KernelParams P, int node, int terms, const double2* x, double2* y) {
+  const NodeDesc nd = P.nodes[node];
+  const TermList L = P.lists[terms];
+  OpStage& os = s_os;
+  const int nt = L.count < TTNS_MAX_TERMS ? L.count : TTNS_MAX_TERMS;
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) os.terms[t] = P.terms[L.first + t];
+  if (threadIdx.x == 0) {
+    os.a_off = os.b_off = 0;
+    os.a_n = os.b_n = 0;
+    os.end = 0;
+  }
+  __syncthreads();
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nd.size;
+       idx += (long long)gridDim.x * blockDim.x)
+    y[idx] = apply_stage2_at<double>(P, nd, x, L, P.work + (long long)P.mmax * P.kvec, P.kvec, idx, os);
+}
+
+cudaError_t launch_apply_x(const KernelParams& P, int node, int terms, int n2, const double2* x, double2* y,
+                           int nblocks, cudaStream_t st) {
+  if (n2 > 0) k_stage1_x<<<nblocks, NT, 0, st>>>(P, node, terms, x);
+  k_apply_x<<<nblocks, NT, 0, st>>>(P, node, terms, x, y);
+  return cudaGetLastError();
 }
 
 // Self-test of the bounded wait: two CTAs; with `skip` set the second CTA never

@@ -29,7 +29,7 @@ EXPORTS = [
     "ttns_node_info", "ttns_get_node", "ttns_save", "ttns_load", "ttns_load_state", "ttns_last_error", "ttns_free",
     "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan", "ttns_selftest_wait_timeout",
     "ttns_rho_from_root_noalloc", "ttns_autotune", "ttns_selftest_tc_gemm", "ttns_mlp_gemm", "ttns_mlp_colsum",
-    "ttns_mlp_diff", "ttns_mlp_adam", "ttns_mlp_status",
+    "ttns_mlp_diff", "ttns_mlp_adam", "ttns_mlp_status", "ttns_energy_surfaces", "ttns_bond_entropies",
 ]
 
 
@@ -96,6 +96,8 @@ def lib():
         L.ttns_occupations.argtypes = [C.c_void_p, C.c_int, dp]
         L.ttns_observables.argtypes = [C.c_void_p, C.c_int, dp, dp]
         L.ttns_trajectory.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, C.POINTER(C.c_int)]
+        L.ttns_energy_surfaces.argtypes = [C.c_void_p, C.c_int, C.c_double, dp, dp, dp, C.POINTER(C.c_int)]
+        L.ttns_bond_entropies.argtypes = [C.c_void_p, C.c_int, dp]
         L.ttns_populations_device.argtypes = [C.c_void_p, C.c_void_p]
         L.ttns_get_counters.argtypes = [C.c_void_p, C.POINTER(Counters)]
         L.ttns_node_info.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -228,6 +230,8 @@ def _options(p0, precision, record=False, max_record=0, stream=None, cluster_cta
         if keep is not None:
             keep.append(arr)
         psi = _dptr(arr)
+    if not qr_cutoff and getattr(p0, "qr_cutoff", None):
+        qr_cutoff = float(p0.qr_cutoff)
     return Options(precision, krylov_tol, krylov_mmax, stream, int(p0.er_tree), int(p0.D_er),
                    int(p0.init_state), psi, int(record), int(max_record), cluster_ctas, grid_ctas,
                    grid_threshold, spin_limit, profile, launch_flags, qr_grid_threshold, qr_cutoff)
@@ -340,6 +344,24 @@ class Tree:
         n = C.c_int()
         _check(lib().ttns_trajectory(self.h, k, _dptr(out), max_steps, C.byref(n)))
         return out[: 2 * n.value * ne * ne].view(np.complex128).reshape(n.value, ne, ne)
+
+    def energy_surfaces(self, k: int = 0, sigma_tol: float = 1e-7):
+        """(total energy surfaces, potential energy surfaces, Schmidt values): the ascending
+        eigenvalues of H_eff and V_eff in the basis of the kept bath states (Eq. 3-4)."""
+        ne = self.problems[k].n_el
+        tes = np.zeros(32)
+        pes = np.zeros(32)
+        sig = np.zeros(ne)
+        nb = C.c_int()
+        _check(lib().ttns_energy_surfaces(self.h, k, sigma_tol, _dptr(tes), _dptr(pes), _dptr(sig), C.byref(nb)))
+        nv = nb.value * ne
+        return tes[:nv].copy(), pes[:nv].copy(), sig[: nb.value].copy()
+
+    def bond_entropies(self, k: int = 0) -> np.ndarray:
+        """[S(rho_S), S(bond of node 1), ..]: von Neumann entropies (natural log)."""
+        out = np.zeros(self.n_nodes(k))
+        _check(lib().ttns_bond_entropies(self.h, k, _dptr(out)))
+        return out
 
     def populations_device(self, dev_ptr: int) -> None:
         _check(lib().ttns_populations_device(self.h, C.c_void_p(dev_ptr)))

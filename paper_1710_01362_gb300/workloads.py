@@ -52,6 +52,7 @@ class Problem:
     psi_el: Optional[np.ndarray] = None  # optional initial electronic amplitudes (n_el complex)
     seed: Optional[int] = None
     notes: str = ""
+    qr_cutoff: Optional[float] = None   # QR null/truncation cutoff (relative); None: 1e-8
 
     @property
     def n_el(self) -> int:
@@ -103,6 +104,7 @@ def batched_spin_boson(seed: int, L: Optional[int] = None, D: Optional[int] = No
     p = spin_boson(eps=delta / 2, V=V, alpha=alpha, omega_c=omega_c, L=Ls, d=d, D=Ds,
                    dt=dt, n_steps=n_steps, name=f"batched_spin_boson_{seed}")
     p.seed = seed
+    p.qr_cutoff = 1e-3
     return p
 
 
@@ -173,9 +175,11 @@ def sf_5state_4x20() -> Problem:
 def sf_er_5state_8x60(L: int = 60, n_steps: int = 800) -> Problem:
     """5 states, balanced binary ER tree over 8 chains of 60 sites (120 modes each),
     local dim 20, bond dim 40, dt 0.25 fs."""
-    return singlet_fission(seed=3, n_env=8, L=L, d=20, D=40, n_modes=120, dt=0.25,
-                           n_steps=n_steps, er_tree=True, D_er=40,
-                           name=f"sf_er_5state_8x{L}_d20_D40")
+    p = singlet_fission(seed=3, n_env=8, L=L, d=20, D=40, n_modes=120, dt=0.25,
+                        n_steps=n_steps, er_tree=True, D_er=40,
+                        name=f"sf_er_5state_8x{L}_d20_D40")
+    p.qr_cutoff = 1e-3
+    return p
 
 
 def sf_small(seed: int = 7, n_env: int = 3, L: int = 5, d: int = 4, D: int = 6,
