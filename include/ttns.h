@@ -118,6 +118,10 @@ typedef struct {
  *   chain_hop       n_env pointers to L_i - 1 hoppings t_in (eV) (may be NULL when L_i == 1)
  *   local_dim       n_env: Fock truncation d_i >= 2 of every site of chain i
  *   bond_dim        n_env: requested bond dimension D_i >= 1 along chain i (and to its parent)
+ *   obb_dim         NULL, or n_env: optimised boson basis dimension of chain i's sites (0: none).
+ *                   With obb_dim[i] > 0 every site of chain i is a tensor joined to a leaf that
+ *                   holds its Fock leg (dimension local_dim) by a bond of dimension obb_dim[i]
+ *                   (Methods: Fock states per mode compressed to a smaller optimised basis)
  * Bond dimensions are clamped to the largest values with D_e <= product of the
  * other leg dimensions at both ends of every bond, so any request at least as large as
  * the Hilbert space (e.g. 1 << 20) asks for the full bond dimension.  A bond that still
@@ -133,6 +137,7 @@ typedef struct {
   const double* const* chain_hop;
   const int* local_dim;
   const int* bond_dim;
+  const int* obb_dim;
 } ttns_problem;
 
 /* Builds one tree and its initial state (electronic state init_state, or psi_el,
@@ -347,6 +352,23 @@ const char* ttns_last_error(void);
 /* Waits for the tree set's stream, then releases every device buffer and the handle.
  * NULL is accepted (no-op).  The handle must not be used afterwards. */
 void ttns_free(ttns_tree* tree);
+
+/* Environments from per-mode couplings (host, FP64; Results, "Interface to TTNS": modes with
+ * similar coupling patterns are grouped by weighted k-means with k-means++ seeding, each
+ * group becomes one chain of Eq. 2).  W: n_modes * n_el * n_el complex, mode n's coupling
+ * matrix W_n (Eq. 1).  Every mode's pattern Wbar_n = W_n / ||W_n||_F is a point of 2 n_el^2
+ * reals with weight ||W_n||_F^2; W and -W are one direction, so a mode meets a centre c
+ * aligned by the sign of <x, c>, at the distance ||x||^2 + ||c||^2 - 2 |<x, c>|.  Lloyd
+ * iterations start from the centres init[0..k) (mode indices, the caller's k-means++ draw),
+ * assign each mode to the nearest centre (ties to the lower index), move each centre to the
+ * weighted mean of its sign-aligned modes (an empty cluster keeps its centre), and stop when
+ * no assignment changes or after max_iter.
+ * Outputs (caller-owned): assign (n_modes cluster indices), W_bar (k * n_el * n_el complex,
+ * the centres at Frobenius norm 1), lambda (n_modes: Re <Wbar_assign(n), W_n>_F, the mode's
+ * strength along its environment's pattern), *iterations.  Feed each environment's modes
+ * (frequencies, lambda) to ttns_chain_from_modes for its chain. */
+ttns_status ttns_cluster_modes(int n_modes, int n_el, const double* W, int k, const int* init, int max_iter,
+                               int* assign, double* W_bar, double* lambda, int* iterations);
 
 /* Chain maps (host, FP64).  ttns_chain_ohmic: closed form for the Ohmic density
  * J(w) = 2 pi alpha w exp(-w/omega_c) (Laguerre weight): ||lambda|| = 2 omega_c

@@ -14,7 +14,10 @@ Tree (Results, "TTNS for vibronic quantum dynamics"; Methods, "Tensor Network St
     is one of its children (chain i, site n+1 is the child of site n);
   * ER form: the electronic node has one child, the top of a balanced binary tree
     of entanglement-renormalisation nodes (third-order tensors, no physical leg);
-    each lowest ER node carries two chains.
+    each lowest ER node carries two chains;
+  * optimised boson basis (Methods: Fock states compressed to a smaller basis per
+    mode): every chain site gets a leaf that holds its Fock leg, joined to the site
+    tensor by a bond of the OBB dimension; the site tensor keeps the chain bonds.
 Each node's legs are ordered [parent bond] + [child bonds, in child order] +
 [physical leg]; tensors are stored row-major in that order.
 
@@ -58,13 +61,13 @@ class Tree:
     parent: List[int]
     children: List[List[int]]
     phys: List[int]                   # 0 = no physical leg
-    kind: List[str]                   # "el", "er", "site"
+    kind: List[str]                   # "el", "er", "site", "obb" (the Fock leaf of a site)
     site_index: List[Optional[Tuple[int, int]]]   # (env, n) for chain sites
     bond: List[int]                   # bond dim to parent (root: 0)
     onsite: List[Optional[np.ndarray]]
     couplings: List[Coupling]
     n_el: int
-    chain_nodes: List[List[int]]      # node ids of chain i, site order
+    chain_nodes: List[List[int]]      # node ids holding chain i's Fock legs, site order
     psi_el: np.ndarray = None
 
     @property
@@ -181,9 +184,18 @@ def build_tree(problem) -> Tree:
         chains.append((rc, om, hop))
         nodes = []
         p = attach[i]
+        obb = getattr(env, "obb", 0) or 0
         for nn in range(env.L):
-            v = add(p, env.d, "site", (i, nn), env.D)
-            nodes.append(v)
+            if obb > 0:
+                # optimised boson basis: the site tensor keeps the chain bonds and a bond of
+                # dimension obb to a leaf that holds the Fock leg (the site's operators act
+                # on the leaf)
+                v = add(p, 0, "site", (i, nn), env.D)
+                leaf = add(v, env.d, "obb", (i, nn), obb)
+                nodes.append(leaf)
+            else:
+                v = add(p, env.d, "site", (i, nn), env.D)
+                nodes.append(v)
             p = v
         chain_nodes.append(nodes)
 

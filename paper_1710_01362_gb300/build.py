@@ -10,7 +10,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libttns.so")
-SOURCES = ["sweep.cu", "capi.cpp", "model.cpp", "noalloc.cu", "tcgemm.cu", "mlp.cu", "observe.cu"]
+SOURCES = ["sweep.cu", "capi.cpp", "model.cpp", "noalloc.cu", "tcgemm.cu", "mlp.cu", "observe.cu",
+           "environments.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(HERE, "..", "include")]
 

@@ -185,6 +185,9 @@ static ttns_status validate(const ttns_problem* p, const ttns_options* opt, Tree
     in->L.push_back(L);
     in->d.push_back(d);
     in->D.push_back(D);
+    const int obb = p->obb_dim ? p->obb_dim[i] : 0;
+    if (obb < 0) return fail(TTNS_E_INVALID, "obb_dim must be >= 0");
+    in->obb.push_back(obb);
   }
   in->er_tree = er;
   in->D_er = er ? opt->D_er : 0;
@@ -1057,6 +1060,7 @@ void write_input(Writer& w, const TreeInput& in) {
   w.put_vec(in.L);
   w.put_vec(in.d);
   w.put_vec(in.D);
+  w.put_vec(in.obb);
   w.put(in.er_tree);
   w.put(in.D_er);
   w.put_vec(in.psi_el);
@@ -1083,6 +1087,7 @@ bool read_input(Reader& r, TreeInput& in) {
   r.get_vec(in.L, kMaxVec);
   r.get_vec(in.d, kMaxVec);
   r.get_vec(in.D, kMaxVec);
+  r.get_vec(in.obb, kMaxVec);
   r.get(in.er_tree);
   r.get(in.D_er);
   r.get_vec(in.psi_el, kMaxVec);
@@ -1091,7 +1096,7 @@ bool read_input(Reader& r, TreeInput& in) {
   const size_t ne = (size_t)in.n_env;
   if (in.n_el < 1 || in.n_el > TTNS_MAX_D || in.n_env < 1 || in.H_S.size() != (size_t)in.n_el * in.n_el ||
       in.W.size() != ne || in.rc.size() != ne || in.omega.size() != ne || in.hop.size() != ne || in.L.size() != ne ||
-      in.d.size() != ne || in.D.size() != ne || in.psi_el.size() != (size_t)in.n_el)
+      in.d.size() != ne || in.D.size() != ne || in.obb.size() != ne || in.psi_el.size() != (size_t)in.n_el)
     return false;
   for (size_t i = 0; i < ne; ++i) {
     if (in.W[i].size() != (size_t)in.n_el * in.n_el || in.L[i] < 1 || in.L[i] > 4096 ||

@@ -172,10 +172,19 @@ HostTree build_host_tree(const TreeInput& in) {
   for (int i = 0; i < in.n_env; ++i) {
     std::vector<int> nodes;
     int p = attach[i];
+    const int obb = (int)in.obb.size() > i ? in.obb[i] : 0;
     for (int s = 0; s < in.L[i]; ++s) {
-      int v = add(p, in.d[i], 2, in.D[i]);
-      nodes.push_back(v);
-      p = v;
+      if (obb > 0) {
+        // optimised boson basis: the site tensor keeps the chain bonds and a bond of dimension
+        // obb to a leaf holding the Fock leg, on which the site's operators act
+        int v = add(p, 0, 2, in.D[i]);
+        nodes.push_back(add(v, in.d[i], 3, obb));
+        p = v;
+      } else {
+        int v = add(p, in.d[i], 2, in.D[i]);
+        nodes.push_back(v);
+        p = v;
+      }
     }
     t.chain_nodes.push_back(nodes);
   }

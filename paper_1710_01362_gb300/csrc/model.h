@@ -25,11 +25,11 @@ struct HostTree {
   std::vector<int> parent;
   std::vector<std::vector<int>> children;
   std::vector<int> phys;             // 0 = no physical leg
-  std::vector<int> kind;             // 0 electronic, 1 ER, 2 chain site
+  std::vector<int> kind;             // 0 electronic, 1 ER, 2 chain site, 3 Fock leaf of a site (OBB)
   std::vector<int> bond;             // bond to parent (root: 0)
   std::vector<std::vector<cplx>> onsite;
   std::vector<Coupling> coups;
-  std::vector<std::vector<int>> chain_nodes;
+  std::vector<std::vector<int>> chain_nodes;  // nodes holding each chain's Fock legs, site order
   std::vector<cplx> psi_el;
 
   int n() const { return (int)parent.size(); }
@@ -48,6 +48,7 @@ struct TreeInput {
   std::vector<double> rc;
   std::vector<std::vector<double>> omega, hop;
   std::vector<int> L, d, D;
+  std::vector<int> obb;              // per env: optimised boson basis dimension (0: none)
   int er_tree = 0;
   int D_er = 0;
   std::vector<cplx> psi_el;

@@ -84,6 +84,7 @@ struct Team {
   int parity;
   Ctl* ctl;
   long long spin_limit;
+  int csize;     // CTAs per thread-block cluster (the grid team reduces per cluster first)
   __device__ int nthr() const { return size * NT; }
   __device__ int gtid() const { return rank * NT + (int)threadIdx.x; }
 };
@@ -676,21 +677,31 @@ __device__ void team_reduce_vec(Team& tm, const double* mine, double* out, int n
       out[k] = a[0];
     }
   } else {
+    // grid team: each cluster first sums its CTAs' partials through distributed shared memory
+    // (the values split over the cluster's CTAs, each value added in a fixed tree), the cluster
+    // totals go to global memory, and after the grid barrier every CTA adds the few cluster
+    // totals in a fixed order.  Every CTA computes the same sums.
+    cg::cluster_group cl = cg::this_cluster();
+    const int cs = tm.csize;
+    const int crank = (int)cl.block_rank();
+    const int cid = tm.rank / cs;
+    const int ncl = tm.size / cs;
     double* buf = team_partials(tm);
-    for (int k = threadIdx.x; k < nval; k += NT) buf[(long long)tm.rank * nval + k] = mine[k];
+    cl.sync();
+    for (int k = crank * NT + threadIdx.x; k < nval; k += cs * NT) {
+      double a[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) a[r] = r < cs ? *cl.map_shared_rank(mine + k, r) : 0.0;
+#pragma unroll
+      for (int w = 8; w >= 1; w >>= 1)
+#pragma unroll
+        for (int r = 0; r < w; ++r) a[r] += a[r + w];
+      buf[(long long)cid * nval + k] = a[0];
+    }
     team_sync(tm);
     for (int k = threadIdx.x; k < nval; k += NT) {
       double s = 0.0;
-      for (int r0 = 0; r0 < tm.size; r0 += 16) {  // blocks of 16 ranks, each added in a tree
-        double a[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) a[r] = r0 + r < tm.size ? buf[(long long)(r0 + r) * nval + k] : 0.0;
-#pragma unroll
-        for (int w = 8; w >= 1; w >>= 1)
-#pragma unroll
-          for (int r = 0; r < w; ++r) a[r] += a[r + w];
-        s += a[0];
-      }
+      for (int c = 0; c < ncl; ++c) s += buf[(long long)c * nval + k];
       out[k] = s;
     }
     tm.parity ^= 1;
@@ -2356,6 +2367,7 @@ __device__ void run(const KernelParams& P, int phase) {
   ct.parity = 0;
   ct.ctl = P.ctl;
   ct.spin_limit = P.spin_limit;
+  ct.csize = cs;
   double2* cwork = P.work + (long long)cluster_id * P.work_stride;
   if (P.batched) {
     for (int tree = cluster_id; tree < P.n_trees; tree += n_clusters) {
@@ -2380,6 +2392,7 @@ __device__ void run(const KernelParams& P, int phase) {
   gt.parity = 0;
   gt.ctl = P.ctl;
   gt.spin_limit = P.spin_limit;
+  gt.csize = cs;
   const TreeDesc& td = P.trees[0];
   const int first = phase == 0 ? td.init_first : (phase == 2 ? td.obs_first : td.prog_first);
   const int count = phase == 0 ? td.init_count : (phase == 2 ? td.obs_count : td.prog_count);

@@ -30,6 +30,7 @@ EXPORTS = [
     "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan", "ttns_selftest_wait_timeout",
     "ttns_rho_from_root_noalloc", "ttns_autotune", "ttns_selftest_tc_gemm", "ttns_mlp_gemm", "ttns_mlp_colsum",
     "ttns_mlp_diff", "ttns_mlp_adam", "ttns_mlp_status", "ttns_energy_surfaces", "ttns_bond_entropies",
+    "ttns_cluster_modes",
 ]
 
 
@@ -55,7 +56,7 @@ class ProblemC(C.Structure):
         ("n_el", C.c_int), ("H_S", C.POINTER(C.c_double)), ("n_env", C.c_int), ("W_bar", C.POINTER(C.c_double)),
         ("rc_coupling", C.POINTER(C.c_double)), ("chain_len", C.POINTER(C.c_int)),
         ("chain_omega", C.POINTER(C.POINTER(C.c_double))), ("chain_hop", C.POINTER(C.POINTER(C.c_double))),
-        ("local_dim", C.POINTER(C.c_int)), ("bond_dim", C.POINTER(C.c_int)),
+        ("local_dim", C.POINTER(C.c_int)), ("bond_dim", C.POINTER(C.c_int)), ("obb_dim", C.POINTER(C.c_int)),
     ]
 
 
@@ -98,6 +99,8 @@ def lib():
         L.ttns_trajectory.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, C.POINTER(C.c_int)]
         L.ttns_energy_surfaces.argtypes = [C.c_void_p, C.c_int, C.c_double, dp, dp, dp, C.POINTER(C.c_int)]
         L.ttns_bond_entropies.argtypes = [C.c_void_p, C.c_int, dp]
+        ip = C.POINTER(C.c_int)
+        L.ttns_cluster_modes.argtypes = [C.c_int, C.c_int, dp, C.c_int, ip, C.c_int, ip, dp, dp, ip]
         L.ttns_populations_device.argtypes = [C.c_void_p, C.c_void_p]
         L.ttns_get_counters.argtypes = [C.c_void_p, C.POINTER(Counters)]
         L.ttns_node_info.argtypes = [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
@@ -160,6 +163,22 @@ def rho_from_root_noalloc(d_root: int, rows: int, n_el: int, d_rho: int, stream:
     _check(lib().ttns_rho_from_root_noalloc(C.c_void_p(d_root), rows, n_el, C.c_void_p(d_rho), C.c_void_p(stream)))
 
 
+def cluster_modes(W: np.ndarray, k: int, init, max_iter: int = 100):
+    """Weighted k-means of the modes' coupling patterns (ttns_cluster_modes): returns
+    (assignment, Wbar (k, n_el, n_el), lambda per mode, iterations)."""
+    Wc = np.ascontiguousarray(W, dtype=np.complex128)
+    n_modes, n_el, _ = Wc.shape
+    ini = np.ascontiguousarray(init, dtype=np.int32)
+    assign = np.zeros(n_modes, dtype=np.int32)
+    Wbar = np.zeros((k, n_el, n_el), dtype=np.complex128)
+    lam = np.zeros(n_modes)
+    it = C.c_int()
+    ip = C.POINTER(C.c_int)
+    _check(lib().ttns_cluster_modes(n_modes, n_el, _dptr(Wc.view(np.float64)), k, ini.ctypes.data_as(ip), max_iter,
+                                    assign.ctypes.data_as(ip), _dptr(Wbar.view(np.float64)), _dptr(lam), C.byref(it)))
+    return assign, Wbar, lam, it.value
+
+
 def chain_ohmic(alpha: float, omega_c: float, L: int):
     rc = np.zeros(1)
     on = np.zeros(L)
@@ -206,9 +225,11 @@ class _ProblemKeep:
         self.hop_ptrs = (C.POINTER(C.c_double) * len(self.hop))(*[_dptr(x) for x in self.hop])
         self.d = np.array([e.d for e in p.envs], dtype=np.int32)
         self.D = np.array([e.D for e in p.envs], dtype=np.int32)
+        self.obb = np.array([getattr(e, "obb", 0) or 0 for e in p.envs], dtype=np.int32)
         self.c = ProblemC(ne, _dptr(self.H), len(p.envs), _dptr(self.W), _dptr(self.rc),
                           self.L.ctypes.data_as(C.POINTER(C.c_int)), self.om_ptrs, self.hop_ptrs,
-                          self.d.ctypes.data_as(C.POINTER(C.c_int)), self.D.ctypes.data_as(C.POINTER(C.c_int)))
+                          self.d.ctypes.data_as(C.POINTER(C.c_int)), self.D.ctypes.data_as(C.POINTER(C.c_int)),
+                          self.obb.ctypes.data_as(C.POINTER(C.c_int)))
 
 
 def current_stream() -> Optional[int]:

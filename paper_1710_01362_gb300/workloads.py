@@ -37,6 +37,7 @@ class Environment:
     L: int                            # chain length (sites)
     d: int                            # local Fock dimension per chain site
     D: int                            # requested bond dimension along this chain
+    obb: int = 0                      # optimised boson basis dimension per site (0: none)
 
 
 @dataclass

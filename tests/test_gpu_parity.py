@@ -347,3 +347,25 @@ def test_bounded_wait_reports_timeout():
     h.step(p.dt, 1)
     h.sync()
     h.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_optimised_boson_basis_tree_matches_oracle(prec):
+    # every chain site joined to a leaf holding its Fock leg by an OBB bond of dimension 2
+    # (Fock dimension 4): the couplings between neighbouring sites run through the site
+    # tensors as dense x dense terms
+    from oracle.ttns import TTNS
+    p = W.sf_small(seed=12, n_env=3, L=3, d=4, D=5, n_modes=8, n_steps=8)
+    for e in p.envs:
+        e.obb = 2
+    g, pops = run_traj(p, p.n_steps, prec)
+    o = TTNS(p)
+    ref = []
+    for _ in range(p.n_steps):
+        o.step(p.dt)
+        ref.append(o.populations())
+    err = np.abs(pops - np.array(ref)).max()
+    assert err < TOL[prec], f"max population error {err:.3e}"
+    np.testing.assert_allclose(g.occupations(), o.occupations(), atol=10 * TOL[prec])
+    assert g.n_nodes() == o.tree.n
+    g.close()

@@ -94,3 +94,46 @@ def test_two_ranks_gloo_batch_equals_single_process():
     single = [_run_tree(p) for p in _problems()]
     for a, b in zip(gathered, single):
         assert np.array_equal(a, b)
+
+
+def _plan_worker(rank, world, port, q):
+    # each rank compiles (host only, ttns_plan in libttns.so) exactly the trees of its shard of
+    # the batched workload, as bench.py's batched run builds them on its GPU; rank 0 gathers
+    # the per-tree bond tables
+    import torch.distributed as dist
+    from paper_1710_01362_gb300 import build, ttns
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        build.build()
+        seeds = list(range(1000, 1000 + 40))
+        lo, hi = shard.shard_range(len(seeds), rank, world)
+        mine = {k: ttns.plan([W.batched_spin_boson(seeds[k])])["bonds"] for k in range(lo, hi)}
+        info = ttns.plan([W.batched_spin_boson(seeds[k]) for k in range(lo, hi)])
+        parts = shard.gather_to_rank0(mine)
+        q.put((rank, lo, hi, info["n_nodes"], parts))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_gloo_plan_the_batched_shards_through_the_library():
+    pytest.importorskip("torch")
+    from paper_1710_01362_gb300 import ttns
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_plan_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    results = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, lo0, hi0, n0, parts0), (r1, lo1, hi1, n1, _) = results
+    assert (lo0, hi0, lo1, hi1) == (0, 20, 20, 40)
+    gathered = shard.merge_shards(parts0, 40)   # every tree planned by exactly one rank
+    whole = ttns.plan([W.batched_spin_boson(s) for s in range(1000, 1040)])
+    assert n0 + n1 == whole["n_nodes"]
+    for k, bonds in enumerate(gathered):
+        assert bonds == ttns.plan([W.batched_spin_boson(1000 + k)])["bonds"]
