@@ -53,8 +53,10 @@ typedef enum {
 } ttns_status;
 
 /* Precision of the contractions (H_eff / H_bond applications and environment updates).  In
- * every mode the Krylov basis and recurrence, the small exponential, the QR bond steps, the
- * gauge absorbs and the observables are FP64.
+ * every mode the Krylov basis and recurrence, the small exponential and the observables are
+ * FP64.  The QR bond steps and the gauge absorbs are FP64 in TTNS_FP64 and double-single
+ * (unevaluated sums of two floats, 48-bit significand, error-free transformations; about
+ * 2^-44 relative per operation, FP32's exponent range) in the other modes.
  *   TTNS_FP64    every contraction in FP64;
  *   TTNS_TF32X3  split-precision tensor cores: the H_eff applications of tensors of at least 4096
  *                elements whose terms have one dense factor each are complex GEMMs on tcgen05 with
@@ -258,6 +260,10 @@ typedef struct {
   /* launches of the persistent kernel that its launch check refused (no planned cluster
    * shape, e.g. under a profiler) and that were repeated as plain cluster launches */
   long long launch_fallbacks;
+  /* phases of the environment updates, [0] cluster and [1] grid teams: 0 operator staging
+   * and operand conversion, 1 the H-term and channel applications, 2 the projection onto
+   * the tensor (per-CTA partials), 3 the team sum of the partials */
+  double env_phase_seconds[2][4];
 } ttns_counters;
 ttns_status ttns_get_counters(ttns_tree* tree, ttns_counters* out);
 

@@ -32,6 +32,7 @@ cudaError_t launch_build_x(const double2* Phi, int k, int l, long long R, int n_
 cudaError_t launch_project(const double2* y, const double2* Phi, long long R, int n_el, int nb, double* partials,
                            int nblocks, double* out, cudaStream_t st);
 cudaError_t launch_sub(const double* a, const double* b, double* c, int n, cudaStream_t st);
+cudaError_t launch_mirror32(const double2* pool, float2* pool32, long long n, cudaStream_t st);
 }  // namespace ttns
 
 using namespace ttns;
@@ -56,6 +57,7 @@ struct ttns_tree {
   cudaStream_t stream = nullptr;
   // device buffers
   double2* pool = nullptr;
+  float2* pool32 = nullptr;  // FP32 mirror of the pool (mixed modes)
   NodeDesc* d_nodes = nullptr;
   Term* d_terms = nullptr;
   TermList* d_lists = nullptr;
@@ -299,9 +301,9 @@ static ttns_status plan_sizes(const Compiled& C, const ttns_options& o, Sizes* z
   if (1 + z->maxchan > z->mmax) return fail(TTNS_E_INVALID, "too many coupling channels for krylov_mmax");
   if (C.max_D > TTNS_MAX_D) return fail(TTNS_E_INVALID, "a bond dimension exceeds 64");
   z->kvec = ((long long)C.max_node + 31) / 32 * 32;
-  // Krylov vectors, two-factor temporaries, the compute-type shadow and a spare slot, and four
-  // slots for the tensor-core group results (up to eight compute-type vectors)
-  z->work_stride = (long long)(z->mmax + std::max(C.max_tmp, 1) + 2 + 4) * z->kvec;
+  // Krylov vectors, two-factor temporaries, the compute-type shadow and a spare slot, and eight
+  // slots for the tensor-core partial results (up to sixteen compute-type vectors)
+  z->work_stride = (long long)(z->mmax + std::max(C.max_tmp, 1) + 2 + 8) * z->kvec;
   long long per_cta = 8;
   per_cta = std::max<long long>(per_cta, 2LL * C.max_D * C.max_D);
   per_cta = std::max<long long>(per_cta, 2LL * (1 + z->maxchan) * C.max_D * C.max_D);
@@ -379,6 +381,10 @@ static ttns_status device_init(ttns_tree* t) {
   const int n_workers = t->batched ? n_clusters : 1;
   if ((s = dalloc(t, &t->pool, C.pool_size)) != TTNS_OK) return s;
   CUDA_TRY(cudaMemcpyAsync(t->pool, C.pool_init.data(), C.pool_size * sizeof(double2), cudaMemcpyHostToDevice, t->stream));
+  if (o.precision != TTNS_FP64) {
+    if ((s = dalloc(t, &t->pool32, C.pool_size)) != TTNS_OK) return s;
+    CUDA_TRY(launch_mirror32(t->pool, t->pool32, C.pool_size, t->stream));
+  }
   if ((s = upload(t, &t->d_nodes, C.nodes)) != TTNS_OK) return s;
   if ((s = upload(t, &t->d_terms, C.terms)) != TTNS_OK) return s;
   if ((s = upload(t, &t->d_lists, C.lists)) != TTNS_OK) return s;
@@ -413,6 +419,7 @@ static ttns_status device_init(ttns_tree* t) {
 
   KernelParams& P = t->P;
   P.pool = t->pool;
+  P.pool32 = t->pool32;
   P.nodes = t->d_nodes;
   P.terms = t->d_terms;
   P.lists = t->d_lists;
@@ -983,6 +990,10 @@ extern "C" ttns_status ttns_get_counters(ttns_tree* t, ttns_counters* out) {
   for (int k = 0; k < 8; ++k) out->qr_phase_seconds[k] = h.phase_cycles[8 + k] / hz;
   for (int k = 0; k < 8; ++k) out->expm_phase_seconds_grid[k] = h.phase_cycles_grid[k] / hz;
   for (int k = 0; k < 8; ++k) out->qr_phase_seconds_grid[k] = h.phase_cycles_grid[8 + k] / hz;
+  for (int k = 0; k < 4; ++k) {
+    out->env_phase_seconds[0][k] = h.phase_cycles[16 + k] / hz;
+    out->env_phase_seconds[1][k] = h.phase_cycles_grid[16 + k] / hz;
+  }
   out->launch_fallbacks = t->launch_fallbacks;
   return TTNS_OK;
 }
@@ -1150,6 +1161,10 @@ ttns_status read_state(ttns_tree* t, FILE* f) {
   h.err_where = 0;
   h.err_node = 0;
   CUDA_TRY(cudaMemcpy(t->pool, pool.data(), pool.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  if (t->pool32) {
+    CUDA_TRY(launch_mirror32(t->pool, t->pool32, (long long)pool.size(), t->stream));
+    CUDA_TRY(cudaStreamSynchronize(t->stream));
+  }
   CUDA_TRY(cudaMemcpy(t->mhist, mh.data(), mh.size() * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->traj_count, tc.data(), tc.size() * sizeof(int), cudaMemcpyHostToDevice));
   CUDA_TRY(cudaMemcpy(t->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));

@@ -121,14 +121,16 @@ struct Ctl {
   int err_node;
   unsigned long long prof_cycles[8][2];  // per op code and team kind (rank-0 CTA clock cycles)
   unsigned long long prof_count[8][2];
-  unsigned long long phase_cycles[16];   // phases of the Krylov exponential (0-7) and QR (8-15), cluster team
-  unsigned long long phase_cycles_grid[16];  // the same for grid-team ops
+  unsigned long long phase_cycles[24];   // phases of the Krylov exponential (0-7), QR (8-15), env (16-19), cluster team
+  unsigned long long phase_cycles_grid[24];  // the same for grid-team ops
   unsigned progress;                     // bumped after every cluster-team instruction
   unsigned pad1;
 };
 
 struct KernelParams {
   double2* pool;           // complex pool
+  float2* pool32;          // FP32 mirror of the pool's operator data (mixed modes; else null):
+                           // written with every operator, read by the compute-type contractions
   const NodeDesc* nodes;
   const Term* terms;
   const TermList* lists;

@@ -103,14 +103,22 @@ __device__ void set_status(Ctl* ctl, int st, int where, int node) {
   }
 }
 
-// software barrier over all CTAs of the grid; bounded
+// software barrier over all CTAs of the grid; bounded.  Hierarchical: the CTAs of each
+// thread-block cluster meet at the hardware cluster barrier, one thread per cluster arrives
+// at the global counter and waits for the generation to change, and a second cluster barrier
+// releases its cluster.  The cluster barriers' release/acquire and the global release/acquire
+// pair order every CTA's writes before the barrier with every CTA's reads after it.  A launch
+// without clusters is a grid of one-CTA clusters.
 __device__ void grid_sync(Ctl* ctl, long long spin_limit) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned csz = cl.num_blocks();
+  if (csz > 1) cl.sync(); else __syncthreads();
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    const unsigned nclu = gridDim.x / csz;
     unsigned g = ld_acquire(&ctl->bar_gen);
     __threadfence();
     unsigned prev = atomicAdd(&ctl->bar_count, 1u);
-    if (prev == gridDim.x - 1) {
+    if (prev == nclu - 1) {
       atomicExch(&ctl->bar_count, 0u);
       __threadfence();
       asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&ctl->bar_gen), "r"(g + 1) : "memory");
@@ -129,12 +137,11 @@ __device__ void grid_sync(Ctl* ctl, long long spin_limit) {
           set_status(ctl, ST_TIMEOUT, 100, -1);
           break;
         }
-        __nanosleep(128);
       }
     }
     __threadfence();
   }
-  __syncthreads();
+  if (csz > 1) cl.sync(); else __syncthreads();
 }
 
 __device__ __forceinline__ void team_sync(Team& tm) {
@@ -335,6 +342,14 @@ __device__ __forceinline__ typename C2<T>::t mode_dot(const MT* row, int D, cons
 // regions.  Matrices stay FP64 (double2) in shared memory and are converted on use.
 extern __shared__ __align__(16) unsigned char dyn_smem[];
 
+// operator data in the compute type: the FP64 pool, or its FP32 mirror
+template <typename T>
+__device__ __forceinline__ const typename C2<T>::t* ops(const KernelParams& P);
+template <>
+__device__ __forceinline__ const double2* ops<double>(const KernelParams& P) { return P.pool; }
+template <>
+__device__ __forceinline__ const float2* ops<float>(const KernelParams& P) { return P.pool32; }
+
 struct OpStage {
   Term terms[TTNS_MAX_TERMS];
   Factor chans[16];
@@ -355,7 +370,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename T>
 __device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& L, const Factor* chans, int nchan,
                          OpStage& os) {
-  const long long cap = P.smem_bytes / (long long)sizeof(double2) / 2;  // half for matrices, half for vectors
+  // half of the dynamic shared memory for matrices (in the compute type), half for vectors
+  using V = typename C2<T>::t;
+  const long long cap = P.smem_bytes / (long long)sizeof(V) / 2;
   __syncthreads();
   if (threadIdx.x == 0) {
     const long long an = I.rega_len < cap ? I.rega_len : cap;
@@ -365,7 +382,9 @@ __device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& 
     os.b_off = I.regb_off;
     os.a_n = (int)an;
     os.b_n = (int)bn;
-    os.end = (int)((an + bn + 1) & ~1LL);
+    // end of the staged matrices in 16-byte units, rounded up to 32 bytes
+    const long long bytes = (an + bn) * (long long)sizeof(V);
+    os.end = (int)((((bytes + 15) / 16) + 1) & ~1LL);
   }
   const int nt = L.count < TTNS_MAX_TERMS ? L.count : TTNS_MAX_TERMS;
   for (int t = threadIdx.x; t < nt; t += NT) os.terms[t] = P.terms[L.first + t];
@@ -377,20 +396,21 @@ __device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& 
     for (int k = threadIdx.x; k < os.b_n; k += NT) cp_async16(sm + os.a_n + k, P.pool + os.b_off + k);
     cp_async_wait_all();
   } else {
-    // converted once here, so that the contractions read compute-type operands (a
-    // double -> float conversion per use would run on the FP64 pipe)
+    // from the FP32 mirror (a double -> float conversion per element would run on the FP64
+    // pipe); the two regions back to back, four loads in flight per thread
     float2* sm = reinterpret_cast<float2*>(dyn_smem);
-    const int nt = os.a_n + os.b_n;  // the two regions back to back, four loads in flight per thread
-    auto src = [&](int k) -> const double2* { return k < os.a_n ? P.pool + os.a_off + k : P.pool + os.b_off + (k - os.a_n); };
+    const int nt = os.a_n + os.b_n;
+    const float2* p32 = P.pool32;
+    auto src = [&](int k) -> const float2* { return k < os.a_n ? p32 + os.a_off + k : p32 + os.b_off + (k - os.a_n); };
     int k = threadIdx.x;
     for (; k + 3 * NT < nt; k += 4 * NT) {
-      const double2 v0 = __ldg(src(k)), v1 = __ldg(src(k + NT)), v2 = __ldg(src(k + 2 * NT)), v3 = __ldg(src(k + 3 * NT));
-      sm[k] = cvt<float>(v0);
-      sm[k + NT] = cvt<float>(v1);
-      sm[k + 2 * NT] = cvt<float>(v2);
-      sm[k + 3 * NT] = cvt<float>(v3);
+      const float2 v0 = *src(k), v1 = *src(k + NT), v2 = *src(k + 2 * NT), v3 = *src(k + 3 * NT);
+      sm[k] = v0;
+      sm[k + NT] = v1;
+      sm[k + 2 * NT] = v2;
+      sm[k + 3 * NT] = v3;
     }
-    for (; k < nt; k += NT) sm[k] = cvt<float>(__ldg(src(k)));
+    for (; k < nt; k += NT) sm[k] = *src(k);
   }
   __syncthreads();
 }
@@ -458,11 +478,11 @@ __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, c
       }
       return acc;
     }
-    const double2* vals = P.pool + f.sp + (long long)lp.i * f.nnz;
-    const double2* cols = P.pool + f.sp + (long long)D * f.nnz + (long long)lp.i * f.nnz;
+    const V* vals = ops<T>(P) + f.sp + (long long)lp.i * f.nnz;
+    const V* cols = ops<T>(P) + f.sp + (long long)D * f.nnz + (long long)lp.i * f.nnz;
     for (int e = 0; e < f.nnz; ++e) {
       const int k = (int)cols[e].x;
-      cmac<T>(acc, cvt<T>(vals[e]), cvt<T>(x[lp.base + (long long)k * nd.strides[f.leg]]));
+      cmac<T>(acc, vals[e], cvt<T>(x[lp.base + (long long)k * nd.strides[f.leg]]));
     }
     return acc;
   }
@@ -471,7 +491,7 @@ __device__ __forceinline__ typename C2<T>::t factor_dot(const KernelParams& P, c
     const typename C2<T>::t* sm = reinterpret_cast<const typename C2<T>::t*>(dyn_smem) + slot;
     return mode_dot<T>(sm + lp.i * D, D, x, lp.base, nd.strides[f.leg]);
   }
-  return mode_dot<T>(P.pool + f.mat + (long long)lp.i * D, D, x, lp.base, nd.strides[f.leg]);
+  return mode_dot<T>(ops<T>(P) + f.mat + (long long)lp.i * D, D, x, lp.base, nd.strides[f.leg]);
 }
 
 // Direct two-factor term at idx: the sparse factor's few entries, each times the dense
@@ -500,14 +520,14 @@ __device__ __forceinline__ typename C2<T>::t direct_dot(const KernelParams& P, c
     }
     return acc;
   }
-  const double2* vals = P.pool + sf.sp + (long long)lp.i * sf.nnz;
-  const double2* cols = P.pool + sf.sp + (long long)Ds * sf.nnz + (long long)lp.i * sf.nnz;
+  const V* vals = ops<T>(P) + sf.sp + (long long)lp.i * sf.nnz;
+  const V* cols = ops<T>(P) + sf.sp + (long long)Ds * sf.nnz + (long long)lp.i * sf.nnz;
   for (int e = 0; e < sf.nnz; ++e) {
-    const double2 v = vals[e];
-    if (v.x == 0.0 && v.y == 0.0) continue;
+    const V v = vals[e];
+    if (v.x == (T)0 && v.y == (T)0) continue;
     const long long idx2 = lp.base + (long long)((int)cols[e].x) * nd.strides[sf.leg];
     const V d = factor_dot<T>(P, nd, df, os, x, idx2);
-    cmac<T>(acc, cvt<T>(v), d);
+    cmac<T>(acc, v, d);
   }
   return acc;
 }
@@ -868,10 +888,10 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
   const int mmax = min(P.mmax, (int)(N < (long long)TTNS_KMAX ? N : (long long)TTNS_KMAX));
   // shared-memory layout after the matrices: [xs: N V][tmp: n2*N V][basis: (mmax+1)*S double2]
   {
-    const long long mats = (long long)(I.rega_len + I.regb_len) * sizeof(double2);
+    const long long mats = (long long)(I.rega_len + I.regb_len) * sizeof(V);
     long long off = (long long)(N + (long long)L.n2 * N) * sizeof(V);
     off = (off + 15) & ~15LL;
-    const long long need = mats + 16 + off + (long long)(mmax + 1) * S * sizeof(double2) + S * (long long)sizeof(V);
+    const long long need = mats + 32 + off + (long long)(mmax + 1) * S * sizeof(double2) + S * (long long)sizeof(V);
     if (need > P.smem_bytes) return false;  // same decision on every CTA (same sizes)
   }
   stage_op<T>(P, I, L, nullptr, 0, os);
@@ -940,10 +960,20 @@ __device__ __noinline__ bool op_expm_cluster(const KernelParams& P, Team& tm, co
         }
       }
       __syncthreads();
-      if (L.n2 > 0) {  // first factors of the two-stage terms, for the whole vector (redundant per CTA)
+      if (L.n2 > 0) {
+        // first factors of the two-stage terms, on the elements that the own slice's second
+        // factors read: the slice widened to whole blocks of the second factor's leg (every
+        // CTA computes its range from the gathered input; for a factor on the last leg the
+        // range is the slice's rows)
         const int t0 = L.count - L.n2;
-        for (long long e = threadIdx.x; e < N; e += NT)
-          for (int t = 0; t < L.n2; ++t) tmp[t * N + e] = factor_dot<T>(P, nd, os.terms[t0 + t].f[0], os, xs, e);
+        for (int t = 0; t < L.n2; ++t) {
+          const int l2 = os.terms[t0 + t].f[1].leg;
+          const long long blk = (long long)nd.dims[l2] * nd.strides[l2];
+          const long long lo = e1 > e0 ? (e0 / blk) * blk : 0;
+          const long long hi = e1 > e0 ? min(N, ((e1 - 1) / blk + 1) * blk) : 0;
+          for (long long e = lo + threadIdx.x; e < hi; e += NT)
+            tmp[t * N + e] = factor_dot<T>(P, nd, os.terms[t0 + t].f[0], os, xs, e);
+        }
         __syncthreads();
       }
       pc.lap(P.ctl, 1);
@@ -1233,7 +1263,10 @@ struct TcPlan {
   int gdense[TTNS_MAX_TERMS];      // index of the dense factor of each grouped term
   int nsimt;
   int simt[TTNS_MAX_TERMS];        // terms evaluated element-wise
-  int gtask0[TTNS_MAX_LEGS + 1];   // first task of group g (tasks of g: row tiles)
+  int gtask0[TTNS_MAX_LEGS + 1];   // first task of group g (tasks of g: K parts x row tiles)
+  int gtiles[TTNS_MAX_LEGS];       // row tiles of group g
+  int gkpart[TTNS_MAX_LEGS];       // complex K per part (whole chunks)
+  int gslot0[TTNS_MAX_LEGS + 1];   // first result slot of group g (one slot per K part)
   float inv_st[TTNS_MAX_LEGS];
 };
 __shared__ TcPlan s_tcp;
@@ -1248,8 +1281,12 @@ __shared__ TcState s_tc;
 
 constexpr int kTcRows = 128;   // rows per task (the MMA's M)
 constexpr int kTcTmemCols = 512;  // all of an SM's tensor memory (one CTA per SM)
+constexpr int kTcSlots = 16;      // compute-type result vectors in the workspace
 
-__device__ void tc_plan(const NodeDesc& nd, const OpStage& os, const TermList& L, TcPlan& tp) {
+// Groups, and each group's K (term, leg index) split into parts of whole chunks, one result
+// slot per part, so that the tasks (group, part, row tile) run on more CTAs and each runs
+// fewer chunks one after another.  ksc: complex K per MMA K step of the precision in use.
+__device__ void tc_plan(const NodeDesc& nd, const OpStage& os, const TermList& L, int ksc, TcPlan& tp) {
   tp.ok = 0;
   if (L.n2 > 0 || L.count > TTNS_MAX_TERMS) return;
   int dleg[TTNS_MAX_TERMS], dfac[TTNS_MAX_TERMS];
@@ -1266,7 +1303,7 @@ __device__ void tc_plan(const NodeDesc& nd, const OpStage& os, const TermList& L
   }
   tp.ngroups = 0;
   tp.nsimt = 0;
-  int nt = 0, ntask = 0;
+  int nt = 0;
   for (int l = 0; l < nd.nl; ++l) {
     int c = 0;
     for (int t = 0; t < L.count; ++t) c += dleg[t] == l;
@@ -1274,15 +1311,32 @@ __device__ void tc_plan(const NodeDesc& nd, const OpStage& os, const TermList& L
     const int g = tp.ngroups++;
     tp.gleg[g] = l;
     tp.gfirst[g] = nt;
-    tp.gtask0[g] = ntask;
     tp.inv_st[g] = 1.0f / (float)nd.strides[l];
     for (int t = 0; t < L.count; ++t)
       if (dleg[t] == l) { tp.gterm[nt] = t; tp.gdense[nt] = dfac[t]; ++nt; }
-    const int rows = nd.size / nd.dims[l];
-    ntask += (rows + kTcRows - 1) / kTcRows;
   }
   tp.gfirst[tp.ngroups] = nt;
+  int ntask = 0, nslot = 0;
+  const int cap = tp.ngroups > 0 ? max(1, kTcSlots / tp.ngroups) : 1;
+  for (int g = 0; g < tp.ngroups; ++g) {
+    const int D = nd.dims[tp.gleg[g]];
+    const int Npad = ((2 * D + 15) / 16) * 16;
+    const int chunk_kc = min(8, kTcTmemCols / Npad) * ksc;
+    const int nterm = tp.gfirst[g + 1] - tp.gfirst[g];
+    const int ktot = ((nterm * D + ksc - 1) / ksc) * ksc;
+    const int nchunk = (ktot + chunk_kc - 1) / chunk_kc;
+    int parts = min(nchunk, cap);
+    const int cpp = (nchunk + parts - 1) / parts;  // chunks per part
+    parts = (nchunk + cpp - 1) / cpp;
+    tp.gkpart[g] = cpp * chunk_kc;
+    tp.gtiles[g] = (nd.size / D + kTcRows - 1) / kTcRows;
+    tp.gtask0[g] = ntask;
+    tp.gslot0[g] = nslot;
+    ntask += parts * tp.gtiles[g];
+    nslot += parts;
+  }
   tp.gtask0[tp.ngroups] = ntask;
+  tp.gslot0[tp.ngroups] = nslot;
   for (int t = 0; t < L.count; ++t)
     if (dleg[t] < 0) tp.simt[tp.nsimt++] = t;
   tp.ok = tp.ngroups > 0;
@@ -1296,13 +1350,13 @@ __device__ __forceinline__ typename C2<T>::t tc_z(const KernelParams& P, const N
   using V = typename C2<T>::t;
   const LegPos lp = leg_pos(nd, fs->leg, idx);
   const int D = nd.dims[fs->leg];
-  const double2* vals = P.pool + fs->sp + (long long)lp.i * fs->nnz;
-  const double2* cols = P.pool + fs->sp + (long long)D * fs->nnz + (long long)lp.i * fs->nnz;
+  const V* vals = ops<T>(P) + fs->sp + (long long)lp.i * fs->nnz;
+  const V* cols = ops<T>(P) + fs->sp + (long long)D * fs->nnz + (long long)lp.i * fs->nnz;
   V acc;
   acc.x = acc.y = (T)0;
   for (int e = 0; e < fs->nnz; ++e) {
     const int k = (int)cols[e].x;
-    cmac<T>(acc, cvt<T>(vals[e]), cvt<T>(x[lp.base + (long long)k * nd.strides[fs->leg]]));
+    cmac<T>(acc, vals[e], cvt<T>(x[lp.base + (long long)k * nd.strides[fs->leg]]));
   }
   return acc;
 }
@@ -1315,8 +1369,8 @@ __device__ __forceinline__ typename C2<T>::t tc_z(const KernelParams& P, const N
 // converted, so their latencies overlap.  Returns false if a completion wait gave up (the
 // status word is set).
 template <int KIND, typename T, typename XT>
-__device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage& os, const TcPlan& tp, int g, int rt,
-                        const XT* x, typename C2<T>::t* yg) {
+__device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage& os, const TcPlan& tp, int g,
+                        int part, int rt, const XT* x, typename C2<T>::t* yg) {
   using S = tc::Split<KIND>;
   using V = typename C2<T>::t;
   TcState& ts = s_tc;
@@ -1346,8 +1400,10 @@ __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage
   const int c_lo = half * (Npad / 2), c_hi = c_lo + Npad / 2;
   for (int c = c_lo; c < c_hi; ++c) sums[my_row * ldsum + c] = 0.0f;
   bool ok = true;
-  for (int kc0 = 0; kc0 < ktot && ok; kc0 += chunk_kc) {
-    const int nk = min(chunk_kc, ktot - kc0);   // a multiple of KSC
+  const int kbeg = part * tp.gkpart[g];
+  const int kend = min(ktot, kbeg + tp.gkpart[g]);
+  for (int kc0 = kbeg; kc0 < kend && ok; kc0 += chunk_kc) {
+    const int nk = min(chunk_kc, kend - kc0);   // a multiple of KSC
     const int Kr = 2 * nk;
     // A: rows of the tile x (term, k) of the chunk
     {
@@ -1401,25 +1457,25 @@ __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage
       const int nitems = (Npad / 2) * per_i;
       for (int item = tid; item < nitems; item += NT) {
         const int kq = item % per_i, i = item / per_i;
-        double2 m[G];
+        float2 m[G];
 #pragma unroll
         for (int j = 0; j < G; ++j) {
           const int kg = kc0 + kq * G + j;
-          m[j] = make_double2(0.0, 0.0);
+          m[j] = make_float2(0.f, 0.f);
           if (i < D && kg < nterm * D) {
             const int tl = kg / D, kk = kg - tl * D;
             const int q = tp.gfirst[g] + tl;
             const Factor& fd = os.terms[tp.gterm[q]].f[tp.gdense[q]];
-            m[j] = P.pool[fd.mat + (long long)i * D + kk];
+            m[j] = P.pool32[fd.mat + (long long)i * D + kk];
           }
         }
 #pragma unroll
         for (int j = 0; j < G; ++j) {
           const int k = kq * G + j;
-          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k, Kr, (float)m[j].x);
-          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k + 1, Kr, (float)-m[j].y);
-          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k, Kr, (float)m[j].y);
-          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k + 1, Kr, (float)m[j].x);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k, Kr, m[j].x);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i, 2 * k + 1, Kr, -m[j].y);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k, Kr, m[j].y);
+          tc::put_split_f<KIND>(B, b_plane, 2 * i + 1, 2 * k + 1, Kr, m[j].x);
         }
       }
     }
@@ -1484,8 +1540,9 @@ __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage
   return true;
 }
 
-// All tasks of the plan over the team's CTAs (task k on rank k mod size).  Y_g at
-// ybuf + g * ystride.  The caller synchronises the team before reading Y.
+// All tasks of the plan over the team's CTAs (task k on rank k mod size).  The result of
+// part p of group g goes to slot gslot0[g] + p at ybuf + slot * ystride.  The caller
+// synchronises the team before reading the slots.
 template <typename T, typename XT>
 __device__ void tc_apply(const KernelParams& P, Team& tm, const NodeDesc& nd, const OpStage& os, const TcPlan& tp,
                          const XT* x, typename C2<T>::t* ybuf, long long ystride) {
@@ -1493,9 +1550,11 @@ __device__ void tc_apply(const KernelParams& P, Team& tm, const NodeDesc& nd, co
   for (int task = tm.rank; task < ntask; task += tm.size) {
     int g = 0;
     while (task >= tp.gtask0[g + 1]) ++g;
-    const int rt = task - tp.gtask0[g];
-    const bool ok = P.precision == 2 ? tc_task<tc::KIND_BF16X3, T>(P, nd, os, tp, g, rt, x, ybuf + g * ystride)
-                                     : tc_task<tc::KIND_TF32X3, T>(P, nd, os, tp, g, rt, x, ybuf + g * ystride);
+    const int local = task - tp.gtask0[g];
+    const int part = local / tp.gtiles[g], rt = local - part * tp.gtiles[g];
+    auto* yg = ybuf + (long long)(tp.gslot0[g] + part) * ystride;
+    const bool ok = P.precision == 2 ? tc_task<tc::KIND_BF16X3, T>(P, nd, os, tp, g, part, rt, x, yg)
+                                     : tc_task<tc::KIND_TF32X3, T>(P, nd, os, tp, g, part, rt, x, yg);
     if (!ok) break;
   }
 }
@@ -1508,8 +1567,9 @@ __device__ __forceinline__ typename C2<T>::t tc_sum_at(const KernelParams& P, co
                                                       long long idx) {
   typename C2<T>::t acc;
   acc.x = acc.y = (T)0;
-  for (int g = 0; g < tp.ngroups; ++g) {
-    const auto y = ybuf[g * ystride + idx];
+  const int nslot = tp.gslot0[tp.ngroups];
+  for (int sl = 0; sl < nslot; ++sl) {
+    const auto y = ybuf[sl * ystride + idx];
     acc.x += y.x;
     acc.y += y.y;
   }
@@ -1544,7 +1604,8 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
   bool use_tc = false;
   if (s_tc.on && (P.precision == 1 || P.precision == 2) && N >= 4096) {
     if (threadIdx.x == 0) {
-      tc_plan(nd, os, L, s_tcp);
+      tc_plan(nd, os, L, P.precision == 2 ? tc::Split<tc::KIND_BF16X3>::kstep / 2 : tc::Split<tc::KIND_TF32X3>::kstep / 2,
+              s_tcp);
       if (s_tcp.ok) {
         os.a_n = os.b_n = 0;
         os.end = 0;
@@ -2156,11 +2217,12 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
     }
   }
   // Q[r][c] = (delta_rc - sum_j V[r][j] Z[j][c]) * ph_c over the own rows, one (c, r) pair
-  // per thread, written back into the tensor
+  // per thread, written back into the tensor; V[r][j] = 0 for j > r and Z[j][c] = 0 for
+  // j > c, so j runs to min(r, c)
   for (int idx = threadIdx.x; idx < n * nr; idx += NT) {
     const int c = fdivu(idx, nr, inv_nr);
     const long long r = rb + (idx - c * nr);
-    const int jmax = (int)(r < (long long)n - 1 ? r : (long long)n - 1);
+    const int jmax = (int)(r < (long long)c ? r : (long long)c);
     double qre = (r == c) ? 1.0 : 0.0, qim = 0.0;
     for (int j = 0; j <= jmax; ++j) {
       if (qs.tau[j] == 0.0) continue;
@@ -2175,6 +2237,8 @@ __device__ __noinline__ void op_qr(const KernelParams& P, Team& tm, const Instr&
   team_sync(tm);
   pc.lap(P.ctl, 12);
 }
+
+#include "qr_ds.cuh"
 
 // ------------------------------------------------------------------ absorb
 // A_u <- R applied on leg I.leg (FP64), through a temporary
@@ -2207,6 +2271,8 @@ __device__ __noinline__ void op_env(const KernelParams& P, Team& tm, const Instr
   const double2* Q = P.pool + nd.off;
   auto* tmp = reinterpret_cast<V*>(work + (long long)P.mmax * kv);
   V* Y = reinterpret_cast<V*>(work);  // Y_0 .. Y_nchan at Y + b*kv, compute type (fits: 1 + nchan <= mmax)
+  PhaseClock pc;
+  pc.start(P.profile && tm.rank == 0 && threadIdx.x == 0, tm.kind == TEAM_GRID);
   const int l = I.leg;
   const int D = I.D;
   const int nb = 1 + I.nchan;
@@ -2227,6 +2293,7 @@ __device__ __noinline__ void op_env(const KernelParams& P, Team& tm, const Instr
   } else {
     xq = reinterpret_cast<const V*>(Q);
   }
+  pc.lap(P.ctl, 16);
   if (L.n2 > 0) {
     apply_stage1<T>(P, tm, nd, xq, L, tmp, kv, os);
     team_sync(tm);
@@ -2236,41 +2303,77 @@ __device__ __noinline__ void op_env(const KernelParams& P, Team& tm, const Instr
     for (int b = 0; b < I.nchan; ++b) Y[(long long)(1 + b) * kv + idx] = factor_dot<T>(P, nd, os.chans[b], os, xq, idx);
   }
   team_sync(tm);
-  // projection: out[b][a][a'] = sum_rows conj(Q[row, a]) Y_b[row, a']
+  pc.lap(P.ctl, 17);
+  // projection: out[b][a][a'] = sum_rows conj(Q[row, a]) Y_b[row, a'].  Each CTA owns a
+  // contiguous block of the output values and sums them over all rows: the rows of an output
+  // are split into `parts` ranges over the CTA's threads (partial sums in the compute type in
+  // runs of 64 rows, then FP64), and one thread per output adds its parts in a fixed order and
+  // writes the value; no partial sums cross CTAs.
   const long long rows = N / D;
   const int nval = nb * D * D;
-  double* part = team_partials(tm);
   const long long lst = nd.strides[l];
-  // rows split across CTAs in contiguous chunks; each thread owns output values
-  const long long chunk = (rows + tm.size - 1) / tm.size;
-  const long long r_begin = (long long)tm.rank * chunk;
-  const long long r_end = min(rows, r_begin + chunk);
-  for (int o = threadIdx.x; o < nval; o += NT) {
+  const int opc = (nval + tm.size - 1) / tm.size;
+  const int ob = min(nval, tm.rank * opc), oe = min(nval, ob + opc);
+  const int nout = oe - ob;
+  const int parts = nout > 0 ? max(1, min(16, NT / nout)) : 1;
+  const long long rpp = (rows + parts - 1) / parts;
+  double2* pbuf = P.cta_scratch + (long long)blockIdx.x * P.cta_scratch_stride;  // parts x nout (parts > 1)
+  double2* out = P.pool + I.env_out;
+  for (int it = threadIdx.x; it < nout * parts; it += NT) {
+    const int o = ob + it % nout, part = it / nout;
     const int b = o / (D * D);
     const int a = (o / D) % D;
     const int a2 = o % D;
     const V* Yb = Y + (long long)b * kv;
+    const long long rb0 = part * rpp, re0 = min(rows, rb0 + rpp);
     double accr = 0, acci = 0;
-    for (long long r0 = r_begin; r0 < r_end; r0 += 64) {
-      V s;
-      s.x = 0;
-      s.y = 0;
-      const long long r1 = min(r_end, r0 + 64);
-      for (long long r = r0; r < r1; ++r) {
-        const long long p = fdivu((int)r, (int)lst, nd.inv_strides[l]), q = r - p * lst;
-        const long long base = p * D * lst + q;
-        const V qa = xq[base + (long long)a * lst];
-        const V y = Yb[base + (long long)a2 * lst];
-        s.x = fma(qa.x, y.x, fma(qa.y, y.y, s.x));
-        s.y = fma(qa.x, y.y, fma(-qa.y, y.x, s.y));
+    for (long long r0 = rb0; r0 < re0; r0 += 64) {
+      V s0, s1;
+      s0.x = s0.y = s1.x = s1.y = 0;
+      const long long r1 = min(re0, r0 + 64);
+      long long r = r0;
+      for (; r + 1 < r1; r += 2) {  // two rows at a time: independent accumulators
+        const long long p0 = fdivu((int)r, (int)lst, nd.inv_strides[l]), q0 = r - p0 * lst;
+        const long long p1 = fdivu((int)(r + 1), (int)lst, nd.inv_strides[l]), q1 = r + 1 - p1 * lst;
+        const long long base0 = p0 * D * lst + q0, base1 = p1 * D * lst + q1;
+        const V qa0 = xq[base0 + (long long)a * lst], y0 = Yb[base0 + (long long)a2 * lst];
+        const V qa1 = xq[base1 + (long long)a * lst], y1 = Yb[base1 + (long long)a2 * lst];
+        s0.x = fma(qa0.x, y0.x, fma(qa0.y, y0.y, s0.x));
+        s0.y = fma(qa0.x, y0.y, fma(-qa0.y, y0.x, s0.y));
+        s1.x = fma(qa1.x, y1.x, fma(qa1.y, y1.y, s1.x));
+        s1.y = fma(qa1.x, y1.y, fma(-qa1.y, y1.x, s1.y));
       }
-      accr += (double)s.x;
-      acci += (double)s.y;
+      if (r < r1) {
+        const long long p0 = fdivu((int)r, (int)lst, nd.inv_strides[l]), q0 = r - p0 * lst;
+        const long long base0 = p0 * D * lst + q0;
+        const V qa0 = xq[base0 + (long long)a * lst], y0 = Yb[base0 + (long long)a2 * lst];
+        s0.x = fma(qa0.x, y0.x, fma(qa0.y, y0.y, s0.x));
+        s0.y = fma(qa0.x, y0.y, fma(-qa0.y, y0.x, s0.y));
+      }
+      accr += (double)s0.x + (double)s1.x;
+      acci += (double)s0.y + (double)s1.y;
     }
-    part[(long long)tm.rank * 2 * nval + 2 * o] = accr;
-    part[(long long)tm.rank * 2 * nval + 2 * o + 1] = acci;
+    if (parts == 1) {
+      out[o] = make_double2(accr, acci);
+      if constexpr (!std::is_same<T, double>::value) P.pool32[I.env_out + o] = make_float2((float)accr, (float)acci);
+    } else
+      pbuf[(long long)part * nout + (o - ob)] = make_double2(accr, acci);  // parts * nout <= NT
   }
-  team_finish_multi(tm, 2 * nval, (double*)(P.pool + I.env_out), 1.0);
+  __syncthreads();
+  pc.lap(P.ctl, 18);
+  if (parts > 1)
+    for (int k = threadIdx.x; k < nout; k += NT) {
+      double sr = 0.0, si = 0.0;
+      for (int part = 0; part < parts; ++part) {
+        const double2 v = pbuf[(long long)part * nout + k];
+        sr += v.x;
+        si += v.y;
+      }
+      out[ob + k] = make_double2(sr, si);
+      if constexpr (!std::is_same<T, double>::value) P.pool32[I.env_out + ob + k] = make_float2((float)sr, (float)si);
+    }
+  team_sync(tm);
+  pc.lap(P.ctl, 19);
   if (tm.rank == 0 && threadIdx.x == 0) {
     atomicAdd(&P.ctl->applies, 1ull);
     atomicAdd(&P.ctl->flops, I.flops);
@@ -2338,13 +2441,19 @@ __device__ void exec_op(const KernelParams& P, Team& tm, const Instr& I, double2
         op_expm<T>(P, tm, I, work, tau);
       break;
     case OP_QR:
-      op_qr(P, tm, I, work);
+      if (P.precision != 0)
+        op_qr_ds(P, tm, I, work);
+      else
+        op_qr(P, tm, I, work);
       break;
     case OP_ENV:
       op_env<T>(P, tm, I, work);
       break;
     case OP_ABSORB:
-      op_absorb(P, tm, I, work);
+      if (P.precision != 0)
+        op_absorb_ds(P, tm, I, work);
+      else
+        op_absorb(P, tm, I, work);
       break;
     case OP_RECORD:
       op_record(P, tm, I, P.traj_count + I.tree);
@@ -2633,6 +2742,19 @@ __global__ void k_wait_selftest(Ctl* ctl, long long spin_limit, int skip) {
 cudaError_t launch_wait_selftest(Ctl* ctl, long long spin_limit, int skip, cudaStream_t st) {
   void* args[] = {&ctl, &spin_limit, &skip};
   return cudaLaunchCooperativeKernel((void*)k_wait_selftest, dim3(2), dim3(NT), args, 0, st);
+}
+
+// FP32 mirror of the pool (after the pool was written from the host)
+__global__ void k_mirror32(const double2* pool, float2* pool32, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    pool32[i] = make_float2((float)pool[i].x, (float)pool[i].y);
+}
+
+cudaError_t launch_mirror32(const double2* pool, float2* pool32, long long n, cudaStream_t st) {
+  long long nb = (n + 255) / 256;
+  nb = nb > 4096 ? 4096 : (nb < 1 ? 1 : nb);
+  k_mirror32<<<(int)nb, 256, 0, st>>>(pool, pool32, n);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ host launch helpers

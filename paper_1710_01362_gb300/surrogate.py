@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import ctypes as C
 import math
+import os
 import time
 from typing import List, Optional, Sequence, Tuple
 
@@ -233,7 +234,8 @@ class Surrogate:
 
 # ------------------------------------------------------------------ end-to-end run
 def run(n_train: int, n_cal: int, n_test: int, n_points: int = 200, epochs: int = 200, batch: int = 256,
-        threshold: float = 1e-3, seed0: int = 100000, cluster_ctas: int = 1, out: Optional[str] = None) -> dict:
+        threshold: float = 1e-3, seed0: int = 100000, cluster_ctas: int = 1, out: Optional[str] = None,
+        data: Optional[str] = None, lr: float = 1e-3, lr_final: float = 1e-5) -> dict:
     """Data from batched TTNS runs (training seeds seed0.., then calibration, then held-out),
     the ensemble trained on the GPU, its held-out error in BF16 inference, and what it gains:
     the held-out parameter sets answered by the network within the threshold, the rest by the
@@ -241,14 +243,24 @@ def run(n_train: int, n_cal: int, n_test: int, n_points: int = 200, epochs: int 
     import json
     import torch
     seeds = list(range(seed0, seed0 + n_train + n_cal + n_test))
-    X, Y, gen_s = generate(seeds, n_points=n_points, cluster_ctas=cluster_ctas)
+    if data and os.path.exists(data):
+        # a dataset written by an earlier run (the same seeds and workload)
+        z = np.load(data)
+        if list(z["seeds"]) != seeds or int(z["n_points"]) != n_points:
+            raise ValueError(f"{data} holds other seeds or trajectory lengths")
+        X, Y, gen_s = z["X"].astype(np.float64), z["Y"].astype(np.float64), float(z["generation_seconds"])
+    else:
+        X, Y, gen_s = generate(seeds, n_points=n_points, cluster_ctas=cluster_ctas)
+        if data:
+            np.savez_compressed(data, X=X, Y=Y.astype(np.float32), seeds=np.array(seeds), n_points=n_points,
+                                generation_seconds=gen_s)
     tr = slice(0, n_train)
     ca = slice(n_train, n_train + n_cal)
     te = slice(n_train + n_cal, n_train + n_cal + n_test)
     sur = Surrogate(n_points=n_points, seed=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sur.fit(X[tr], Y[tr], X[ca], Y[ca], epochs=epochs, batch=batch)
+    sur.fit(X[tr], Y[tr], X[ca], Y[ca], epochs=epochs, batch=batch, lr=lr, lr_final=lr_final)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     t0 = time.perf_counter()
@@ -290,7 +302,12 @@ if __name__ == "__main__":
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--threshold", type=float, default=1e-3)
     ap.add_argument("--cluster-ctas", type=int, default=1)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=1e-5)
+    ap.add_argument("--data", default="", help=".npz dataset: read if present, else written")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
-    print(json.dumps(run(a.n_train, a.n_cal, a.n_test, a.n_points, a.epochs, threshold=a.threshold,
-                         cluster_ctas=a.cluster_ctas, out=a.out or None), indent=1))
+    print(json.dumps(run(a.n_train, a.n_cal, a.n_test, a.n_points, a.epochs, batch=a.batch, threshold=a.threshold,
+                         cluster_ctas=a.cluster_ctas, out=a.out or None, data=a.data or None, lr=a.lr,
+                         lr_final=a.lr_final), indent=1))

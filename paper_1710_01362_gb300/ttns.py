@@ -73,7 +73,8 @@ class Counters(C.Structure):
                 ("not_converged", C.c_longlong), ("steps", C.c_longlong), ("op_seconds", (C.c_double * 2) * 6),
                 ("op_count", (C.c_longlong * 2) * 6), ("expm_phase_seconds", C.c_double * 8),
                 ("qr_phase_seconds", C.c_double * 8), ("expm_phase_seconds_grid", C.c_double * 8),
-                ("qr_phase_seconds_grid", C.c_double * 8), ("launch_fallbacks", C.c_longlong)]
+                ("qr_phase_seconds_grid", C.c_double * 8), ("launch_fallbacks", C.c_longlong),
+                ("env_phase_seconds", (C.c_double * 4) * 2)]
 
 
 _lib = None
@@ -403,9 +404,12 @@ class Tree:
         phases_g = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm"],
                             [c.expm_phase_seconds_grid[k] for k in range(7)]))
         qr_g = dict(zip(qr_names, [c.qr_phase_seconds_grid[k] for k in range(8)]))
+        env_names = ["staging", "apply", "projection", "team_sum"]
         return {"krylov_iters": c.krylov_iters, "applies": c.applies, "contraction_flops": c.contraction_flops,
                 "not_converged": c.not_converged, "steps": c.steps, "profile": prof, "expm_phases": phases,
                 "qr_phases": qr, "expm_phases_grid": phases_g, "qr_phases_grid": qr_g,
+                "env_phases": dict(zip(env_names, [c.env_phase_seconds[0][k] for k in range(4)])),
+                "env_phases_grid": dict(zip(env_names, [c.env_phase_seconds[1][k] for k in range(4)])),
                 "launch_fallbacks": c.launch_fallbacks}
 
     def n_nodes(self, k: int = 0) -> int:

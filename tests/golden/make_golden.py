@@ -36,23 +36,51 @@ CASES = {
 for s in range(1000, 1016):
     CASES[f"batched_spin_boson_{s}"] = ((lambda s=s: W.batched_spin_boson(s)), 60, 10)
 
-# Sensitivity envelopes: the same oracle with a tighter Krylov tolerance.  Two correct
-# runs of a well-conditioned trajectory agree to ~1e-10; these runs measure it for the
-# workloads whose bonds fill up during the run (QR cutoff 1e-3).
-TIGHT = {f"batched_spin_boson_{s}_tol14": (f"batched_spin_boson_{s}", 1e-14) for s in range(1000, 1004)}
+# Sensitivity envelopes of the trajectories themselves, from the oracle alone:
+#   *_tol14:  the same run with the Krylov tolerance 1e-14 instead of 1e-12 (differences at
+#             the FP64 rounding level: what an FP64 implementation can be held to);
+#   *_noise7: the same run with relative Gaussian noise of 1e-7 added to every H v and
+#             environment application (seeded; the FP32 level of the mixed-precision
+#             contractions).
+# A well-conditioned trajectory keeps both small; where the trajectory amplifies them (a
+# kept sub-column near the QR cutoff steers the one-site tangent space), two correct runs
+# differ by the envelope, and parity is judged against it.
+TIGHT = {f"batched_spin_boson_{s}_tol14": (f"batched_spin_boson_{s}", 1e-14) for s in range(1000, 1016)}
 TIGHT["sf_er_5state_8x12_d20_D40_tol14"] = ("sf_er_5state_8x12_d20_D40", 1e-14)
 TIGHT["sf_5state_4x20_d10_D20_tol14"] = ("sf_5state_4x20_d10_D20", 1e-14)
+NOISY = {f"batched_spin_boson_{s}_noise7": (f"batched_spin_boson_{s}", 1e-7) for s in range(1000, 1016)}
+NOISY["sf_er_5state_8x12_d20_D40_noise7"] = ("sf_er_5state_8x12_d20_D40", 1e-7)
+
+
+def _noisy_apply(level: float, seed: int = 123):
+    """TTNS.apply_terms with relative Gaussian noise of the given level on every result."""
+    rng = np.random.default_rng(seed)
+    plain = TTNS.apply_terms
+
+    def noisy(A, terms):
+        y = plain(A, terms)
+        s = np.sqrt(np.mean(np.abs(y) ** 2)) if y.size else 0.0
+        return y + level * s * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape)) / np.sqrt(2)
+    return plain, noisy
 
 
 def run_case(name: str) -> None:
     tol = None
+    noise = 0.0
     if name in TIGHT:
         base, tol = TIGHT[name]
+        factory, n_steps, occ_every = CASES[base]
+    elif name in NOISY:
+        base, noise = NOISY[name]
         factory, n_steps, occ_every = CASES[base]
     else:
         factory, n_steps, occ_every = CASES[name]
     p = factory()
     st = TTNS(p) if tol is None else TTNS(p, tol=tol)
+    plain = None
+    if noise > 0.0:
+        plain, noisy = _noisy_apply(noise)
+        TTNS.apply_terms = staticmethod(noisy)
     pops = [st.populations().tolist()]
     occ = {0: st.occupations().tolist()}
     t0 = time.time()
@@ -74,6 +102,9 @@ def run_case(name: str) -> None:
         "stats": st.stats,
         "oracle_seconds": time.time() - t0,
     }
+    if plain is not None:
+        TTNS.apply_terms = staticmethod(plain)
+        out["noise"] = noise
     with open(os.path.join(HERE, name + ".json"), "w") as f:
         json.dump(out, f, separators=(",", ":"))
     print(name, "done in", round(time.time() - t0, 1), "s", flush=True)

@@ -1,7 +1,9 @@
 """The oracle's own conditioning on the workloads whose GPU parity is checked over long
-horizons: the stored trajectories at Krylov tolerance 1e-12 and 1e-14 (both written by
-tests/golden/make_golden.py from oracle/) must agree to 1e-9 at every step, so that a
-1e-6 / 1e-7 parity bound means something at every step.  Reads stored files only."""
+horizons, from stored trajectories only (all written by tests/golden/make_golden.py from
+oracle/): the run at Krylov tolerance 1e-12, the same at 1e-14 (the FP64 rounding level),
+and the same with relative noise 1e-7 on every application (the FP32 level).  The GPU
+parity tests bound their errors by the tolerance plus ten times these envelopes; these
+tests pin what the envelopes are."""
 import json
 import os
 
@@ -9,14 +11,40 @@ import numpy as np
 import pytest
 
 GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+BATCHED = [f"batched_spin_boson_{s}" for s in range(1000, 1016)]
 
 
-@pytest.mark.parametrize("name", ["sf_er_5state_8x12_d20_D40"] + [f"batched_spin_boson_{s}" for s in range(1000, 1004)])
-def test_krylov_tolerance_envelope_is_tiny(name):
-    paths = [os.path.join(GOLD, name + ".json"), os.path.join(GOLD, name + "_tol14.json")]
-    if not all(os.path.exists(p) for p in paths):
+def pops(name):
+    path = os.path.join(GOLD, name + ".json")
+    if not os.path.exists(path):
         pytest.skip("golden trajectories not generated")
-    a, b = [np.array(json.load(open(p))["populations"]) for p in paths]
-    assert np.abs(a - b).max() < 1e-9
-    # populations of a normalised state
-    assert np.abs(a.sum(axis=1) - 1).max() < 1e-10
+    return np.array(json.load(open(path))["populations"])
+
+
+@pytest.mark.parametrize("name", ["sf_er_5state_8x12_d20_D40"] + BATCHED)
+def test_envelopes_of_normalised_runs(name):
+    for suffix in ("", "_tol14", "_noise7"):
+        a = pops(name + suffix)
+        assert np.abs(a.sum(axis=1) - 1).max() < 1e-10  # populations of a normalised state
+        assert a.min() > -1e-10
+
+
+def test_fp64_envelope_is_tiny_except_one_tree():
+    """At the FP64 rounding level 15 of the 16 batched trees and the ER tree stay below
+    1e-9; seed 1010 amplifies it to ~3e-7 after step 40."""
+    big = {}
+    for name in ["sf_er_5state_8x12_d20_D40"] + BATCHED:
+        d = np.abs(pops(name) - pops(name + "_tol14")).max()
+        if d >= 1e-9:
+            big[name] = d
+    assert list(big) == ["batched_spin_boson_1010"]
+    assert big["batched_spin_boson_1010"] < 1e-6
+
+
+def test_fp32_envelope():
+    """At the FP32 level 14 of 16 batched trees stay below 1e-6 over 60 steps; seeds 1010 and
+    1012 do not, and the ER tree stays below 1e-7 for its first 20 steps."""
+    over = [name for name in BATCHED if np.abs(pops(name) - pops(name + "_noise7")).max() >= 1e-6]
+    assert sorted(over) == ["batched_spin_boson_1010", "batched_spin_boson_1012"]
+    er = np.abs(pops("sf_er_5state_8x12_d20_D40") - pops("sf_er_5state_8x12_d20_D40_noise7")).max(axis=1)
+    assert er[:21].max() < 1e-7
