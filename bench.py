@@ -333,6 +333,45 @@ def roofline(res, prec_name, world):
             "issued_tensor_flops_factor": 6 if prec_name == "bf16x3" else (3 if prec_name == "tf32x3" else 0)}
 
 
+def precision_study(name, prec, pname, N, stream, lf, torch, ttns):
+    """The workload run N steps in the given precision and in FP64 on the GPU, one after the
+    other: the largest population difference at every step (reported per eighth of the run),
+    the occupations every N/8 steps, and both paths' device time per step."""
+    p = make_problems(name)[0]
+    every = max(1, N // 8)
+    runs = {}
+    for label, pr in ((pname, prec), ("fp64", ttns.TTNS_FP64)):
+        with torch.cuda.stream(stream):
+            t = ttns.Tree(p, precision=pr, record=True, max_record=N, stream=stream.cuda_stream, launch_flags=lf)
+            occ, ms = [], 0.0
+            done = 0
+            while done < N:
+                n = min(every, N - done)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                t.step(p.dt, n)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b)
+                done += n
+                occ.append(t.occupations())
+            tr = t.trajectory(max_steps=N)
+            runs[label] = dict(pops=np.real(np.einsum("kii->ki", tr)), occ=np.array(occ), ms_per_step=ms / N,
+                               norm_dev=float(np.abs(np.real(np.einsum("kii->k", tr)) - 1).max()))
+            t.close()
+    a, b = runs[pname], runs["fp64"]
+    d = np.abs(a["pops"] - b["pops"]).max(axis=1)
+    docc = np.abs(a["occ"] - b["occ"]).reshape(len(a["occ"]), -1).max(axis=1)
+    return {"study": "precision", "workload": name, "steps": N, "dt_fs": p.dt, "precision": pname,
+            "max_pop_diff": float(d.max()), "max_pop_diff_per_eighth": [float(x) for x in d.reshape(-1, every).max(axis=1)]
+            if N % every == 0 else [float(d.max())],
+            "max_occ_diff": float(docc.max()), "occ_diff_every": every, "max_occ_diff_per_eighth": docc.tolist(),
+            "max_occupation": float(b["occ"].max()),
+            "ms_per_step": {pname: a["ms_per_step"], "fp64": b["ms_per_step"]},
+            "trace_dev": {pname: a["norm_dev"], "fp64": b["norm_dev"]},
+            "populations_end": {pname: a["pops"][-1].tolist(), "fp64": b["pops"][-1].tolist()}}
+
+
 def run_batched(name, prec, K, Wm, dev, stream, lf, torch, shard, ttns, rank, world):
     """256 independent trees split by tree across the ranks; value = tree-sweeps of all ranks
     over the slowest rank's time."""
@@ -374,6 +413,9 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--plain-cluster-launch", action="store_true",
                     help="launch the persistent kernel without the cooperative attribute (profiler runs)")
+    ap.add_argument("--precision-study", type=int, default=0, metavar="N",
+                    help="instead of the benchmark: N steps of the workload in its precision and in FP64, "
+                         "populations of every step and occupations every N/8 steps compared (one JSON line)")
     args = ap.parse_args()
     spec = WORKLOADS[args.workload]
     if args.steps <= 0:
@@ -411,6 +453,12 @@ def main():
             print(json.dumps(out), flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
+        return
+
+    if args.precision_study > 0:
+        if rank == 0:
+            print(json.dumps(precision_study(args.workload, prec, pname, args.precision_study, stream, lf, torch, ttns)),
+                  flush=True)
         return
 
     res = run_single(args.workload, prec, K, Wm, dev, stream, lf, torch, shard, ttns, world)

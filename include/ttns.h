@@ -247,8 +247,9 @@ typedef struct {
   double op_seconds[6][2];
   long long op_count[6][2];
   /* phases of the cluster-team Krylov exponentials: 0 operator staging, 1 first
-   * factors of two-factor terms, 2 apply + alpha reduction, 3 recurrence + beta
-   * reduction, 4 small exponential / convergence, 5 final combination, 6 norm */
+   * factors of two-factor terms, 2 apply + alpha reduction (with the tensor-core path:
+   * the pass that sums the result slots), 3 recurrence + beta reduction, 4 small
+   * exponential / convergence, 5 final combination, 6 norm, 7 tensor-core tasks */
   double expm_phase_seconds[8];
   /* phases of the cluster-team QRs: 0 copy + norm, 1 column loop (its team reductions),
    * 2 Gram of the reflectors, 3 T and Z, 4 Q and R written back, and inside the column
@@ -264,6 +265,9 @@ typedef struct {
    * and operand conversion, 1 the H-term and channel applications, 2 the projection onto
    * the tensor (per-CTA partials), 3 the team sum of the partials */
   double env_phase_seconds[2][4];
+  /* phases of the tensor-core tasks run by the team's first CTA: 0 operand staging, 1 MMA
+   * issue and completion, 2 tensor-memory read-back and sums, 3 result write */
+  double tc_phase_seconds[4];
 } ttns_counters;
 ttns_status ttns_get_counters(ttns_tree* tree, ttns_counters* out);
 

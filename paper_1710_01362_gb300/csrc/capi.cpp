@@ -16,7 +16,8 @@ namespace ttns {
 cudaError_t launch_sweep(const KernelParams& P, int phase, int grid, int cluster, int cooperative,
                          cudaStream_t stream);
 cudaError_t max_grid_for(int cluster, long long smem_bytes, int* grid);
-cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double* partials,
+cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double2* xbuf,
+                           double* partials,
                            int nblocks, double* out, cudaStream_t st);
 cudaError_t launch_energy(const KernelParams& P, int node, int terms, int n2, double* partials, int nblocks,
                           double* out, cudaStream_t st);
@@ -667,8 +668,9 @@ static int find_root_fwd_terms(ttns_tree* t, int tree_idx, int* n2) {
 static ttns_status density(ttns_tree* t, int node, int leg, const double2* rho_in, double* out) {
   const NodeDesc& nd = t->C.nodes[node];
   const int D = nd.dims[leg];
-  int nblocks = (int)std::min<long long>(1024, std::max<long long>(1, nd.size / D / 64));
-  CUDA_TRY(launch_density(t->pool, nd, leg, rho_in, t->obs, nblocks, out, t->stream));
+  // about eight rows per block; rho_in applied once per element into the worker workspace
+  int nblocks = (int)std::min<long long>(1024, std::max<long long>(1, nd.size / D / 8));
+  CUDA_TRY(launch_density(t->pool, nd, leg, rho_in, t->work, t->obs, nblocks, out, t->stream));
   return TTNS_OK;
 }
 
@@ -993,6 +995,7 @@ extern "C" ttns_status ttns_get_counters(ttns_tree* t, ttns_counters* out) {
   for (int k = 0; k < 4; ++k) {
     out->env_phase_seconds[0][k] = h.phase_cycles[16 + k] / hz;
     out->env_phase_seconds[1][k] = h.phase_cycles_grid[16 + k] / hz;
+    out->tc_phase_seconds[k] = h.phase_cycles_grid[20 + k] / hz;
   }
   out->launch_fallbacks = t->launch_fallbacks;
   return TTNS_OK;

@@ -37,8 +37,8 @@
 #define TTNS_NOALLOC_SCRATCH_DOUBLES (TTNS_NOALLOC_MAX_BLOCKS * 2 * TTNS_NOALLOC_MAX_NEL * TTNS_NOALLOC_MAX_NEL)
 
 namespace ttns {
-cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double* partials,
-                           int nblocks, double* out, cudaStream_t st);
+cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double2* xbuf,
+                           double* partials, int nblocks, double* out, cudaStream_t st);
 void set_last_error(const std::string& msg);
 }  // namespace ttns
 
@@ -103,7 +103,7 @@ extern "C" ttns_status ttns_rho_from_root_noalloc(const double* d_root, long lon
   long long nb = rows / 64;
   if (nb < 1) nb = 1;
   if (nb > TTNS_NOALLOC_MAX_BLOCKS) nb = TTNS_NOALLOC_MAX_BLOCKS;
-  e = ttns::launch_density(reinterpret_cast<const double2*>(d_root), nd, 1, nullptr, scratch, (int)nb, d_rho,
+  e = ttns::launch_density(reinterpret_cast<const double2*>(d_root), nd, 1, nullptr, nullptr, scratch, (int)nb, d_rho,
                            static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) {
     ttns::set_last_error(std::string("ttns_rho_from_root_noalloc: launch: ") + cudaGetErrorString(e));

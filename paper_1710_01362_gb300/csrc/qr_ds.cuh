@@ -476,53 +476,65 @@ __device__ __noinline__ void op_qr_ds(const KernelParams& P, Team& tm, const Ins
     }
     team_reduce_vec_ds(tm, mine, redo, 2 * npair);
   }
-  // G (FP64) in the partial buffer that the last reduction's barrier released
-  double2* G = reinterpret_cast<double2*>(red[rp]);
+  // Gram of the unit reflectors, Gd[a][b] = shat_a shat_b (reduced sum), a <= b, double-single,
+  // in the partial buffer that the last reduction's barrier released
+  float4* Gd = reinterpret_cast<float4*>(red[rp]);
   for (int p = threadIdx.x; p < npair; p += NT) {
     int b = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
     while ((b + 1) * (b + 2) / 2 <= p) ++b;
     while (b * (b + 1) / 2 > p) --b;
     const int a = p - b * (b + 1) / 2;
-    const double sab = qs.shat[a] * qs.shat[b];
-    G[a * n + b] = make_double2(sab * ds_to(redo[2 * p]), sab * ds_to(redo[2 * p + 1]));
+    const float2 sab = ds_from(qs.shat[a] * qs.shat[b]);
+    DsAcc gr, gi;
+    gr.init(make_float2(0.f, 0.f));
+    gi.init(make_float2(0.f, 0.f));
+    gr.mac(sab, redo[2 * p]);
+    gi.mac(sab, redo[2 * p + 1]);
+    Gd[a * n + b] = ds_c(gr.val(), gi.val());
   }
+  // T (upper triangular, double-single, in the storage of Tm): T[j][j] = 2, T[0:j, j] =
+  // -2 T[0:j, 0:j] G[0:j, j] (rows and columns of identity reflectors stay zero); four lanes
+  // per row i split the dot and add by shuffles.  Ts[i][j] = shat_i T[i][j] shat_j for Z.
+  float4* Td = reinterpret_cast<float4*>(Tm);
   for (int idx = threadIdx.x; idx < n * n; idx += NT) {
-    Tm[idx / n * ldg + idx % n] = make_double2(0, 0);
+    Td[idx / n * ldg + idx % n] = make_float4(0.f, 0.f, 0.f, 0.f);
     Ts[idx / n * ldg + idx % n] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   __syncthreads();
   pc.lap(P.ctl, 10);
-  // T (FP64, upper triangular): T[j][j] = 2, T[0:j, j] = -2 T[0:j, 0:j] G[0:j, j]; the scaled
-  // copy Ts[i][j] = shat_i T[i][j] shat_j in double-single for Z
-  for (int j = 0; j < n; ++j) {
-    const double tj = qs.tau[j] != 0.0 ? 2.0 : 0.0;
-    if (threadIdx.x < j && tj != 0.0) {
-      const int i = threadIdx.x;
-      double sr0 = 0, si0 = 0, sr1 = 0, si1 = 0;
-      int k = i;
-      for (; k + 1 < j; k += 2) {
-        const double2 t0 = Tm[i * ldg + k], g0 = G[k * n + j];
-        const double2 t1 = Tm[i * ldg + k + 1], g1 = G[(k + 1) * n + j];
-        sr0 = fma(t0.x, g0.x, fma(-t0.y, g0.y, sr0));
-        si0 = fma(t0.x, g0.y, fma(t0.y, g0.x, si0));
-        sr1 = fma(t1.x, g1.x, fma(-t1.y, g1.y, sr1));
-        si1 = fma(t1.x, g1.y, fma(t1.y, g1.x, si1));
+  {
+    const int i = threadIdx.x >> 2, q = threadIdx.x & 3;
+    for (int j = 0; j < n; ++j) {
+      const bool tj = qs.tau[j] != 0.0;
+      const bool on = tj && i < j;
+      DsAcc sr, si;
+      sr.init(make_float2(0.f, 0.f));
+      si.init(make_float2(0.f, 0.f));
+      if (on)
+        for (int k = i + q; k < j; k += 4) ds_cmac(sr, si, Td[i * ldg + k], Gd[k * n + j]);
+      float2 vr = sr.val(), vi = si.val();
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {  // within the aligned group of four lanes
+        vr = ds_add(vr, shfl_xor_ds(vr, o));
+        vi = ds_add(vi, shfl_xor_ds(vi, o));
       }
-      if (k < j) {
-        const double2 t0 = Tm[i * ldg + k], g0 = G[k * n + j];
-        sr0 = fma(t0.x, g0.x, fma(-t0.y, g0.y, sr0));
-        si0 = fma(t0.x, g0.y, fma(t0.y, g0.x, si0));
+      if (on && q == 0) {
+        const float4 t = make_float4(-2.f * vr.x, -2.f * vr.y, -2.f * vi.x, -2.f * vi.y);  // exact
+        Td[i * ldg + j] = t;
+        const float2 sij = ds_from(qs.shat[i] * qs.shat[j]);
+        DsAcc a, b;
+        a.init(make_float2(0.f, 0.f));
+        b.init(make_float2(0.f, 0.f));
+        a.mac(sij, ds_re(t));
+        b.mac(sij, ds_im(t));
+        Ts[i * ldg + j] = ds_c(a.val(), b.val());
       }
-      const double2 t = make_double2(-tj * (sr0 + sr1), -tj * (si0 + si1));
-      Tm[i * ldg + j] = t;
-      const double s = qs.shat[i] * qs.shat[j];
-      Ts[i * ldg + j] = ds_cfrom(make_double2(s * t.x, s * t.y));
+      if (threadIdx.x == 0 && tj) {
+        Td[j * ldg + j] = make_float4(2.f, 0.f, 0.f, 0.f);
+        Ts[j * ldg + j] = ds_c(ds_from(2.0 * qs.shat[j] * qs.shat[j]), make_float2(0.f, 0.f));
+      }
+      __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      Tm[j * ldg + j] = make_double2(tj, 0.0);
-      Ts[j * ldg + j] = ds_cfrom(make_double2(tj * qs.shat[j] * qs.shat[j], 0.0));
-    }
-    __syncthreads();
   }
   // Z[j][c] = sum_{j <= i <= c} Ts[j][i] conj(V[c][i]) (upper triangular), so that
   // Q = I - V Z with the unnormalised V of the workspace

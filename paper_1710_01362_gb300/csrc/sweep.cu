@@ -365,6 +365,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename T>
@@ -397,20 +401,11 @@ __device__ void stage_op(const KernelParams& P, const Instr& I, const TermList& 
     cp_async_wait_all();
   } else {
     // from the FP32 mirror (a double -> float conversion per element would run on the FP64
-    // pipe); the two regions back to back, four loads in flight per thread
+    // pipe) with asynchronous 8-byte copies: every copy of a thread is in flight at once
     float2* sm = reinterpret_cast<float2*>(dyn_smem);
-    const int nt = os.a_n + os.b_n;
-    const float2* p32 = P.pool32;
-    auto src = [&](int k) -> const float2* { return k < os.a_n ? p32 + os.a_off + k : p32 + os.b_off + (k - os.a_n); };
-    int k = threadIdx.x;
-    for (; k + 3 * NT < nt; k += 4 * NT) {
-      const float2 v0 = *src(k), v1 = *src(k + NT), v2 = *src(k + 2 * NT), v3 = *src(k + 3 * NT);
-      sm[k] = v0;
-      sm[k + NT] = v1;
-      sm[k + 2 * NT] = v2;
-      sm[k + 3 * NT] = v3;
-    }
-    for (; k < nt; k += NT) sm[k] = *src(k);
+    for (int k = threadIdx.x; k < os.a_n; k += NT) cp_async8(sm + k, P.pool32 + os.a_off + k);
+    for (int k = threadIdx.x; k < os.b_n; k += NT) cp_async8(sm + os.a_n + k, P.pool32 + os.b_off + k);
+    cp_async_wait_all();
   }
   __syncthreads();
 }
@@ -454,6 +449,14 @@ __device__ void stage_vector(typename C2<T>::t* dst, const double2* src, long lo
     dst[k + 3 * NT] = cvt<T>(d);
   }
   for (; k < N; k += NT) dst[k] = cvt<T>(src[k]);
+  __syncthreads();
+}
+
+// A compute-type vector copied into shared memory with asynchronous copies.
+__device__ void stage_copy(float2* dst, const float2* src, long long N) {
+  __syncthreads();
+  for (long long k = threadIdx.x; k < N; k += NT) cp_async8(dst + k, src + k);
+  cp_async_wait_all();
   __syncthreads();
 }
 
@@ -1369,8 +1372,10 @@ __device__ __forceinline__ typename C2<T>::t tc_z(const KernelParams& P, const N
 // converted, so their latencies overlap.  Returns false if a completion wait gave up (the
 // status word is set).
 template <int KIND, typename T, typename XT>
-__device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage& os, const TcPlan& tp, int g,
-                        int part, int rt, const XT* x, typename C2<T>::t* yg) {
+__device__ __noinline__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage& os, const TcPlan& tp, int g,
+                        int part, int rt, const XT* x, typename C2<T>::t* yg, bool prof) {
+  PhaseClock pc;  // phases 20-23 (grid counters): operand staging, MMA completion, read-back, write
+  pc.start(prof && threadIdx.x == 0, true);
   using S = tc::Split<KIND>;
   using V = typename C2<T>::t;
   TcState& ts = s_tc;
@@ -1481,6 +1486,7 @@ __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage
     }
     tc::fence_proxy_async();
     __syncthreads();
+    pc.lap(P.ctl, 20);
     const int nsteps = nk / KSC;
     if (tid == 0) {
       tc::fence_after();
@@ -1493,23 +1499,32 @@ __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage
     ok = __syncthreads_and(w) != 0;  // the same decision on every thread
     if (!ok) break;
     if (tid == 0) ts.phase ^= 1u;
-    // the K steps' partial products, summed in a fixed order into the shared FP32 sums
+    pc.lap(P.ctl, 21);
+    // the K steps' partial products, summed in a fixed order into the shared FP32 sums; the
+    // loads of all K steps of a column group are issued before one wait
     const uint32_t lane_base = ts.tmem + ((uint32_t)(q4 * 32) << 16);
     for (int c = c_lo; c < c_hi; c += 8) {
+      uint32_t r[8][8];
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks)
+        if (ks < nsteps) tc::tmem_ld8_nowait(lane_base + (uint32_t)(ks * Npad + c), r[ks]);
+      tc::tmem_wait_ld();
       float acc[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[j] = 0.0f;
-      for (int ks = 0; ks < nsteps; ++ks) {
-        float v[8];
-        tc::tmem_ld8(lane_base + (uint32_t)(ks * Npad + c), v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j] += v[j];
-      }
+      for (int ks = 0; ks < 8; ++ks)
+        if (ks < nsteps) {
+          tc::tmem_pin8(r[ks]);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[j] += __uint_as_float(r[ks][j]);
+        }
 #pragma unroll
       for (int j = 0; j < 8; ++j) sums[my_row * ldsum + c + j] += acc[j];
     }
     tc::fence_before();
     __syncthreads();
+    pc.lap(P.ctl, 22);
   }
   if (!ok) {
     // a completion wait gave up: report it, give the MMAs in flight a last bounded wait, and
@@ -1537,6 +1552,7 @@ __device__ bool tc_task(const KernelParams& P, const NodeDesc& nd, const OpStage
     }
   }
   __syncthreads();
+  pc.lap(P.ctl, 23);
   return true;
 }
 
@@ -1553,8 +1569,9 @@ __device__ void tc_apply(const KernelParams& P, Team& tm, const NodeDesc& nd, co
     const int local = task - tp.gtask0[g];
     const int part = local / tp.gtiles[g], rt = local - part * tp.gtiles[g];
     auto* yg = ybuf + (long long)(tp.gslot0[g] + part) * ystride;
-    const bool ok = P.precision == 2 ? tc_task<tc::KIND_BF16X3, T>(P, nd, os, tp, g, part, rt, x, yg)
-                                     : tc_task<tc::KIND_TF32X3, T>(P, nd, os, tp, g, part, rt, x, yg);
+    const bool prof = P.profile && tm.rank == 0;
+    const bool ok = P.precision == 2 ? tc_task<tc::KIND_BF16X3, T>(P, nd, os, tp, g, part, rt, x, yg, prof)
+                                     : tc_task<tc::KIND_TF32X3, T>(P, nd, os, tp, g, part, rt, x, yg, prof);
     if (!ok) break;
   }
 }
@@ -1618,9 +1635,11 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
   V* xs = use_tc ? nullptr : vec_smem<T>(P, os, N);  // input vector in shared memory when it fits
   // otherwise, in mixed precision, a compute-type copy of the input vector in the workspace,
   // written by the pass that produces the vector (FP64 Krylov basis, FP32 operand)
+  // (kept in the mixed modes whether or not the vector is staged: staging then copies it
+  // instead of converting the FP64 vector on every CTA)
   constexpr bool kShadow = !std::is_same<T, double>::value;
   V* xf = reinterpret_cast<V*>(work + (long long)(P.mmax + P.n_tmp) * kv);
-  const bool shadow = kShadow && xs == nullptr;
+  const bool shadow = kShadow;
   // tiled apply for a grid-team node that does not fit in shared memory
   TiledApply& tp = s_tp;
   V* xt = nullptr;
@@ -1674,7 +1693,12 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
       const double sj = ks.scale[j];
       const double bj = ks.beta[j];
       const double sjm = j > 0 ? ks.scale[j - 1] : 0.0;
-      if (xs) stage_vector<T>(xs, Kj, N);
+      if (xs) {
+        if constexpr (kShadow)
+          stage_copy(xs, xf, N);
+        else
+          stage_vector<T>(xs, Kj, N);
+      }
       // operand of this application: shared memory, the FP32 shadow, or K_j itself (FP64)
       const V* xin = xs ? xs : (shadow ? xf : reinterpret_cast<const V*>(Kj));
       if (L.n2 > 0) {
@@ -1704,6 +1728,7 @@ __device__ __noinline__ void op_expm(const KernelParams& P, Team& tm, const Inst
       if (use_tc) {
         tc_apply<T>(P, tm, nd, os, s_tcp, xin, ybuf, kv);
         team_sync(tm);
+        pc.lap(P.ctl, 7);
         for (long long idx = tm.gtid(); idx < N; idx += tm.nthr())
           recur(idx, tc_sum_at<T>(P, nd, os, s_tcp, xin, ybuf, kv, idx));
       } else if (tiled) {
@@ -2578,16 +2603,36 @@ __global__ void __launch_bounds__(NT, 1) k_sweep(KernelParams P, int phase) {
 //   out[b][b'] = sum rho_in[p', p] A[p, .., b, ..] conj(A[p', .., b', ..]) over the other legs.
 // One CTA per call (small sizes), except that the root (rho_in == nullptr) may be large:
 // a grid of CTAs writes partials, reduced by k_reduce_partials.
-__global__ void k_density_partial(const double2* pool, NodeDesc nd, int l, const double2* rho_in, double* partials) {
+// X = rho_in applied on leg 0 of the node tensor: X[idx] = sum_a' rho_in[a'][a] A[.., a', ..]
+// with a the leg-0 index of idx (the incoming parent-bond density of a downward pass)
+__global__ void k_apply_rho0(const double2* A, NodeDesc nd, const double2* rho_in, double2* X) {
+  const int Dp = nd.dims[0];
+  const long long stp = nd.strides[0];
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nd.size;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int qa = fdivu((int)idx, (int)stp, nd.inv_strides[0]);
+    const int a = qa - fdivu(qa, Dp, nd.inv_dims[0]) * Dp;
+    const long long b0 = idx - (long long)a * stp;
+    double xr = 0.0, xi = 0.0;
+    for (int a2 = 0; a2 < Dp; ++a2) {
+      const double2 r_ = rho_in[a2 * Dp + a];
+      const double2 v = A[b0 + (long long)a2 * stp];
+      xr = fma(r_.x, v.x, fma(-r_.y, v.y, xr));
+      xi = fma(r_.x, v.y, fma(r_.y, v.x, xi));
+    }
+    X[idx] = make_double2(xr, xi);
+  }
+}
+
+// partials of rho[b][b2] = sum_rows X[row, b] conj(A[row, b2]) along leg l, rows split over
+// the blocks (X = A for the root)
+__global__ void k_density_partial(const double2* X, const double2* A, NodeDesc nd, int l, double* partials) {
   const int D = nd.dims[l];
   const long long N = nd.size;
   const long long st = nd.strides[l];
   const long long rows = N / D;
   const long long chunk = (rows + gridDim.x - 1) / gridDim.x;
   const long long r_begin = (long long)blockIdx.x * chunk, r_end = min(rows, r_begin + chunk);
-  const double2* A = pool + nd.off;
-  const int Dp = rho_in ? nd.dims[0] : 0;
-  const long long stp = nd.strides[0];
   for (int o = threadIdx.x; o < D * D; o += blockDim.x) {
     const int b = o / D, b2 = o % D;
     double accr = 0, acci = 0;
@@ -2595,23 +2640,7 @@ __global__ void k_density_partial(const double2* pool, NodeDesc nd, int l, const
       const long long p = fdivu((int)r, (int)st, nd.inv_strides[l]), q = r - p * st;
       const long long base = p * D * st + q;
       const double2 y = A[base + (long long)b2 * st];
-      double2 xa;
-      if (!rho_in) {
-        xa = A[base + (long long)b * st];
-      } else {
-        // X[idx] = sum_a' rho_in[a'][a] A[a', ...] evaluated at idx = base + b*st (a = parent index)
-        const long long idx = base + (long long)b * st;
-        const int qa = fdivu((int)idx, (int)stp, nd.inv_strides[0]);
-        const int a = qa - fdivu(qa, Dp, nd.inv_dims[0]) * Dp;
-        const long long b0 = idx - (long long)a * stp;
-        xa = make_double2(0, 0);
-        for (int a2 = 0; a2 < Dp; ++a2) {
-          const double2 r_ = rho_in[a2 * Dp + a];
-          const double2 v = A[b0 + (long long)a2 * stp];
-          xa.x += r_.x * v.x - r_.y * v.y;
-          xa.y += r_.x * v.y + r_.y * v.x;
-        }
-      }
+      const double2 xa = X[base + (long long)b * st];
       accr = fma(xa.x, y.x, fma(xa.y, y.y, accr));
       acci = fma(xa.y, y.x, fma(-xa.x, y.y, acci));
     }
@@ -2822,9 +2851,17 @@ cudaError_t max_grid_for(int cluster, long long smem_bytes, int* grid) {
   return cudaSuccess;
 }
 
-cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double* partials,
-                           int nblocks, double* out, cudaStream_t st) {
-  k_density_partial<<<nblocks, NT, 0, st>>>(pool, nd, l, rho_in, partials);
+cudaError_t launch_density(const double2* pool, const NodeDesc& nd, int l, const double2* rho_in, double2* xbuf,
+                           double* partials, int nblocks, double* out, cudaStream_t st) {
+  const double2* A = pool + nd.off;
+  const double2* X = A;
+  if (rho_in) {
+    long long nb = (nd.size + NT - 1) / NT;
+    nb = nb > 4096 ? 4096 : nb;
+    k_apply_rho0<<<(int)nb, NT, 0, st>>>(A, nd, rho_in, xbuf);
+    X = xbuf;
+  }
+  k_density_partial<<<nblocks, NT, 0, st>>>(X, A, nd, l, partials);
   const int D = nd.dims[l];
   k_reduce_partials<<<(2 * D * D + NT - 1) / NT, NT, 0, st>>>(partials, nblocks, 2 * D * D, out);
   return cudaGetLastError();

@@ -74,7 +74,7 @@ class Counters(C.Structure):
                 ("op_count", (C.c_longlong * 2) * 6), ("expm_phase_seconds", C.c_double * 8),
                 ("qr_phase_seconds", C.c_double * 8), ("expm_phase_seconds_grid", C.c_double * 8),
                 ("qr_phase_seconds_grid", C.c_double * 8), ("launch_fallbacks", C.c_longlong),
-                ("env_phase_seconds", (C.c_double * 4) * 2)]
+                ("env_phase_seconds", (C.c_double * 4) * 2), ("tc_phase_seconds", C.c_double * 4)]
 
 
 _lib = None
@@ -397,12 +397,12 @@ class Tree:
             for k, team in enumerate(["grid", "cluster"]):
                 if c.op_count[op][k]:
                     prof[f"{names[op]}_{team}"] = (c.op_seconds[op][k], c.op_count[op][k])
-        phases = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm"],
-                          [c.expm_phase_seconds[k] for k in range(7)]))
+        phases = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm", "tc_tasks"],
+                          [c.expm_phase_seconds[k] for k in range(8)]))
         qr_names = ["copy_norm", "columns", "gram", "T_Z", "write_Q", "col_reflector", "col_update", "col_dots"]
         qr = dict(zip(qr_names, [c.qr_phase_seconds[k] for k in range(8)]))
-        phases_g = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm"],
-                            [c.expm_phase_seconds_grid[k] for k in range(7)]))
+        phases_g = dict(zip(["staging", "stage1", "apply_alpha", "recurrence_beta", "small_expm", "combine", "norm", "tc_tasks"],
+                            [c.expm_phase_seconds_grid[k] for k in range(8)]))
         qr_g = dict(zip(qr_names, [c.qr_phase_seconds_grid[k] for k in range(8)]))
         env_names = ["staging", "apply", "projection", "team_sum"]
         return {"krylov_iters": c.krylov_iters, "applies": c.applies, "contraction_flops": c.contraction_flops,
@@ -410,6 +410,7 @@ class Tree:
                 "qr_phases": qr, "expm_phases_grid": phases_g, "qr_phases_grid": qr_g,
                 "env_phases": dict(zip(env_names, [c.env_phase_seconds[0][k] for k in range(4)])),
                 "env_phases_grid": dict(zip(env_names, [c.env_phase_seconds[1][k] for k in range(4)])),
+                "tc_phases": dict(zip(["staging", "mma", "readback", "write"], [c.tc_phase_seconds[k] for k in range(4)])),
                 "launch_fallbacks": c.launch_fallbacks}
 
     def n_nodes(self, k: int = 0) -> int:

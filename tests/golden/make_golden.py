@@ -50,6 +50,7 @@ TIGHT["sf_er_5state_8x12_d20_D40_tol14"] = ("sf_er_5state_8x12_d20_D40", 1e-14)
 TIGHT["sf_5state_4x20_d10_D20_tol14"] = ("sf_5state_4x20_d10_D20", 1e-14)
 NOISY = {f"batched_spin_boson_{s}_noise7": (f"batched_spin_boson_{s}", 1e-7) for s in range(1000, 1016)}
 NOISY["sf_er_5state_8x12_d20_D40_noise7"] = ("sf_er_5state_8x12_d20_D40", 1e-7)
+NOISY["sf_5state_4x20_d10_D20_noise7"] = ("sf_5state_4x20_d10_D20", 1e-7)
 
 
 def _noisy_apply(level: float, seed: int = 123):

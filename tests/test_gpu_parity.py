@@ -15,9 +15,11 @@ only: the same trajectory at Krylov tolerance 1e-14 (the FP64 rounding level) an
 relative noise 1e-7 on every application (the FP32 level).  Most of these trajectories keep
 both envelopes far below the tolerances; a few amplify them (a kept sub-column near the
 cutoff steers the one-site tangent space), and there two correct runs differ by the
-envelope.  These tests therefore bound the GPU at step k by
-    TOL + 10 * envelope_k       (envelope: tol14 for FP64, noise7 for mixed)
-and hold every tree whose envelope stays below TOL / 2 for the whole run to TOL alone.
+envelope.  These tests therefore hold every trajectory whose envelope (tol14 for FP64,
+noise7 for the mixed modes) stays below TOL / 2 for the whole run to TOL alone; any other
+is held to TOL until the onset of its ill-conditioned stretch (envelope above TOL / 10)
+and to TOL + 10 x (largest envelope after the onset) from there on: two correct runs
+diverge there at times that depend on the perturbation.
 """
 import json
 import os
@@ -104,16 +106,22 @@ def envelope(name, prec):
 
 
 def check_against_envelope(label, err, env, tol):
-    """err, env: per-step arrays.  Every step within tol + 10 env; a run whose envelope stays
-    below tol / 2 is held to tol alone.  Returns whether the strict rule applied."""
-    bound = tol + 10.0 * env
-    bad = np.nonzero(err > bound)[0]
-    assert bad.size == 0, (f"{label}: step {bad[0] + 1} error {err[bad[0]]:.3e} above "
-                           f"{tol:.0e} + 10 x envelope {env[bad[0]]:.3e}")
-    strict = env.max() < tol / 2
-    if strict:
+    """err, env: per-step arrays.  A run whose envelope stays below tol / 2 is held to tol at
+    every step.  Otherwise it is held to tol until the onset of its ill-conditioned stretch
+    (the first step where the envelope exceeds tol / 10), and from there on to tol plus ten
+    times the largest envelope of the rest of the run (two correct runs diverge there at
+    times that depend on the perturbation, so the bound is not taken step by step).
+    Returns whether the strict rule applied to the whole run."""
+    if env.max() < tol / 2:
         assert err.max() < tol, f"{label}: max population error {err.max():.3e}"
-    return strict
+        return True
+    onset = int(np.argmax(env > tol / 10)) if (env > tol / 10).any() else len(env)
+    assert err[:onset].max(initial=0.0) < tol, (f"{label}: error {err[:onset].max():.3e} before the onset "
+                                                f"(step {onset + 1}) of the envelope")
+    late = tol + 10.0 * env[onset:].max(initial=0.0)
+    assert err[onset:].max(initial=0.0) < late, (f"{label}: error {err[onset:].max():.3e} after step {onset} above "
+                                                 f"{late:.3e}")
+    return False
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -163,8 +171,9 @@ def test_batched_with_many_trees_equals_single_runs():
 @pytest.mark.parametrize("prec", PRECS)
 def test_singlet_fission_4x20_full_trajectory(prec):
     """The 4 x 20 star tree at full size: 5 states, 4 chains x 20 sites, d 10, D 20, 400
-    steps of 0.5 fs, every population of every step and the chain occupations at the end
-    compared with the oracle."""
+    steps of 0.5 fs, every population of every step (the envelope rule over the 400 steps
+    when the oracle's envelope runs are stored, else the stated tolerance) and the chain
+    occupations at the end compared with the oracle."""
     name = "sf_5state_4x20_d10_D20"
     gd = golden(name)
     p = W.sf_5state_4x20()
@@ -173,9 +182,16 @@ def test_singlet_fission_4x20_full_trajectory(prec):
     ref = np.array(gd["populations"])[1:]
     err = np.abs(pops - ref).max(axis=1)
     print(f"max population error {err.max():.3e} (first 50 steps {err[:50].max():.3e})")
-    assert err.max() < TOL[prec], f"max population error {err.max():.3e}"
+    suffix = "_tol14" if prec == ttns.TTNS_FP64 else "_noise7"
+    if os.path.exists(os.path.join(GOLD, name + suffix + ".json")):
+        env = envelope(name, prec)
+        check_against_envelope(name, err, env, TOL[prec])
+        occ_tol = 10 * (TOL[prec] + 10 * env.max())
+    else:
+        assert err.max() < TOL[prec], f"max population error {err.max():.3e}"
+        occ_tol = 10 * TOL[prec]
     occ = g.occupations()
-    np.testing.assert_allclose(occ, gd["occupations"][str(n)], atol=10 * TOL[prec])
+    np.testing.assert_allclose(occ, gd["occupations"][str(n)], atol=occ_tol)
     g.close()
 
 
@@ -183,7 +199,7 @@ def test_singlet_fission_4x20_full_trajectory(prec):
 def test_er_tree_8x12_reduced_length(prec):
     """The ER-tree workload (5 states, 7 ER nodes, 8 chains, d 20, D 40, QR cutoff 1e-3) at
     the reduced chain length 12: every population of 40 steps against the oracle (the stated
-    tolerance while the oracle's envelope is below half of it, the envelope rule after),
+    tolerance until the onset of the oracle's envelope, the envelope rule after),
     and the occupations at steps 10, 20, 30 and 40."""
     name = "sf_er_5state_8x12_d20_D40"
     gd = golden(name)
@@ -202,7 +218,7 @@ def test_er_tree_8x12_reduced_length(prec):
     ref = np.array(gd["populations"])[1:]
     err = np.abs(pops - ref).max(axis=1)
     check_against_envelope(name, err, env, TOL[prec])
-    calm = np.nonzero(np.maximum.accumulate(env) < TOL[prec] / 2)[0]
+    calm = np.nonzero(np.maximum.accumulate(env) < TOL[prec] / 10)[0]
     print(f"max population error {err.max():.3e}; strict over the first {calm.size} steps: {err[calm].max():.3e}")
     assert calm.size >= 20 and err[calm].max() < TOL[prec]
     g.close()
