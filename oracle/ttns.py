@@ -41,7 +41,7 @@ from typing import Dict, List, Optional, Tuple
 import numpy as np
 
 from .linalg import expm_lanczos, householder_qr, KRYLOV_TOL, KRYLOV_MMAX
-from .model import Coupling, Tree, build_tree, initial_tensors, lowering
+from .model import Coupling, Tree, _clamp_bonds, build_tree, initial_tensors, lowering
 
 HBAR = 0.6582119569  # eV fs
 
@@ -244,6 +244,57 @@ class TTNS:
         self._visit(0, 0.5 * dt)
         self._visit_adj(0, 0.5 * dt)
         self.t += dt
+
+    # ------------------------------------------------------------------ adaptive bond dimension
+    def grow_bonds(self, new_bond) -> List[int]:
+        """Raises bond dimensions during the run (the paper raises them until the dynamics
+        converge; Methods, tensor network states).  new_bond[v] is the requested dimension of
+        node v's parent bond; the root's entry and requests not above the current dimension
+        leave a bond as it is, and the requests go through the build's clamp.  The state is
+        unchanged:
+          * both tensors of a grown bond get zero slices on it;
+          * grown bonds are taken children first: the child's tensor is made an isometry
+            toward its parent again by this module's QR, whose zero columns get the identity
+            reflector (the completion rule), and R (the identity on the old indices, zero on
+            the new ones) is absorbed into the parent;
+          * every environment is rebuilt.
+        Taking children first leaves each parent's completion for later, so no absorb acts on
+        a completed tensor.  The new bond directions are the completion vectors, which the
+        one-site integrator can then populate.  Returns the grown nodes."""
+        tr = self.tree
+        req = [0] + [max(tr.bond[v], int(new_bond[v])) for v in range(1, tr.n)]
+        nb = _clamp_bonds(tr, req)
+        nb[0] = 0
+        grown = [v for v in range(1, tr.n) if nb[v] > tr.bond[v]]
+        if not grown:
+            return []
+        tr.bond = nb
+        for v in range(tr.n):
+            shape = tuple(tr.legs(v))
+            if shape != self.A[v].shape:
+                B = np.zeros(shape, dtype=complex)
+                B[tuple(slice(0, k) for k in self.A[v].shape)] = self.A[v]
+                self.A[v] = B
+        for v in sorted(grown, reverse=True):
+            p = tr.parent[v]
+            R = self.qr_toward(v, p)
+            self.absorb(R, p, v)
+        self.env = {}
+        self._init_envs()
+        return grown
+
+    def bond_spectra(self) -> Dict[int, np.ndarray]:
+        """Ascending eigenvalues (Schmidt weights) of every parent bond's density matrix."""
+        return {v: np.linalg.eigvalsh(0.5 * (rho + rho.conj().T)) for v, rho in self.bond_densities().items()}
+
+    def adapt_bonds(self, eps: float, step: int, d_max: int) -> List[int]:
+        """Adaptive rule: a parent bond below d_max whose smallest Schmidt weight exceeds eps
+        uses all of its dimension; it grows by `step`, up to d_max (then the build's clamp)."""
+        new = [0] * self.tree.n
+        for v, w in self.bond_spectra().items():
+            if self.tree.bond[v] < d_max and w[0] > eps:
+                new[v] = min(self.tree.bond[v] + step, d_max)
+        return self.grow_bonds(new)
 
     # ------------------------------------------------------------------ observables
     def norm(self) -> float:
