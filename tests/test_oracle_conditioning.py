@@ -21,7 +21,7 @@ def pops(name):
     return np.array(json.load(open(path))["populations"])
 
 
-@pytest.mark.parametrize("name", ["sf_er_5state_8x12_d20_D40"] + BATCHED)
+@pytest.mark.parametrize("name", ["sf_er_5state_8x12_d20_D40", "sf_5state_4x20_d10_D20"] + BATCHED)
 def test_envelopes_of_normalised_runs(name):
     for suffix in ("", "_tol14", "_noise7"):
         a = pops(name + suffix)
@@ -48,3 +48,13 @@ def test_fp32_envelope():
     assert sorted(over) == ["batched_spin_boson_1010", "batched_spin_boson_1012"]
     er = np.abs(pops("sf_er_5state_8x12_d20_D40") - pops("sf_er_5state_8x12_d20_D40_noise7")).max(axis=1)
     assert er[:21].max() < 1e-7
+
+
+def test_star_tree_4x20_is_ill_conditioned_over_400_steps():
+    """At the default cutoff 1e-8 the 400-step 4 x 20 trajectory stays calm for its first
+    steps and then amplifies both perturbations (its parity test uses the envelope rule)."""
+    a = pops("sf_5state_4x20_d10_D20")
+    t14 = np.abs(a - pops("sf_5state_4x20_d10_D20_tol14")).max(axis=1)
+    n7 = np.abs(a - pops("sf_5state_4x20_d10_D20_noise7")).max(axis=1)
+    assert t14[:10].max() < 1e-9 and n7[:10].max() < 1e-7
+    assert t14.max() > 1e-6 and n7.max() > 1e-4
