@@ -355,6 +355,9 @@ def precision_study(name, prec, pname, N, stream, lf, torch, ttns):
                 ms += a.elapsed_time(b)
                 done += n
                 occ.append(t.occupations())
+                # progress (a partial record survives an interrupted run)
+                print(json.dumps({"study_progress": label, "steps_done": done, "ms_per_step": ms / done,
+                                  "populations": t.populations().tolist()}), flush=True)
             tr = t.trajectory(max_steps=N)
             runs[label] = dict(pops=np.real(np.einsum("kii->ki", tr)), occ=np.array(occ), ms_per_step=ms / N,
                                norm_dev=float(np.abs(np.real(np.einsum("kii->k", tr)) - 1).max()))

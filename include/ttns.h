@@ -224,6 +224,26 @@ ttns_status ttns_energy_surfaces(ttns_tree* tree, int tree_idx, double sigma_tol
  * Node numbering as in ttns_node_info.  S_out holds n_nodes doubles (caller-owned). */
 ttns_status ttns_bond_entropies(ttns_tree* tree, int tree_idx, double* S_out);
 
+/* Adaptive bond dimension (the paper raises bond dimensions until the dynamics converge;
+ * Methods, tensor network states).  Single-tree sets only (else TTNS_E_INVALID).
+ * new_bond[v] (v = 0 .. n_nodes - 1, host, caller-owned) is the requested dimension of node v's
+ * parent bond; the root's entry and requests not above the current dimension leave a bond as
+ * it is, and the requests go through the build's Hilbert-space clamp (a bond above 64 after it
+ * gives TTNS_E_INVALID and leaves the tree as it was).  Every grown bond gets zero slices in
+ * both of its tensors; grown bonds are taken children first, the child's tensor is made an
+ * isometry toward its parent again by the sweep's QR (its zero columns get the identity
+ * reflector: the completion rule of the step) and R is absorbed into the parent; then every
+ * environment block is rebuilt.  The state, the time, the trajectory record and the counters
+ * carry over; the device memory of the tree set is reallocated (the handle stays valid).
+ * n_grown (optional) receives the number of grown bonds.  Synchronising. */
+ttns_status ttns_grow_bonds(ttns_tree* tree, const int* new_bond, int n_nodes, int* n_grown);
+
+/* The adaptive rule: every parent bond below d_max whose smallest Schmidt weight (eigenvalue
+ * of the bond's density matrix, from the downward pass) exceeds eps uses all of its dimension
+ * and grows by `step`, up to d_max, through ttns_grow_bonds.  eps >= 0, step >= 1 and
+ * d_max >= 1, else TTNS_E_INVALID. */
+ttns_status ttns_adapt_bonds(ttns_tree* tree, double eps, int step, int d_max, int* n_grown);
+
 /* Copies the recorded rho_S trajectory of tree tree_idx: out holds
  * max_steps*n_el*n_el complex; *n_written receives the number of steps copied. */
 ttns_status ttns_trajectory(ttns_tree* tree, int tree_idx, double* out, int max_steps, int* n_written);

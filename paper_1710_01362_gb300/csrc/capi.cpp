@@ -34,6 +34,8 @@ cudaError_t launch_project(const double2* y, const double2* Phi, long long R, in
                            int nblocks, double* out, cudaStream_t st);
 cudaError_t launch_sub(const double* a, const double* b, double* c, int n, cudaStream_t st);
 cudaError_t launch_mirror32(const double2* pool, float2* pool32, long long n, cudaStream_t st);
+cudaError_t launch_pad_copy(const double2* src_pool, const NodeDesc& so, double2* dst_pool, const NodeDesc& dn,
+                            cudaStream_t st);
 }  // namespace ttns
 
 using namespace ttns;
@@ -768,11 +770,14 @@ static ttns_status eig_batch(ttns_tree* t, const double2* base, const std::vecto
 
 // The environment pass of the chains' kinetic energy (persistent kernel, phase 2), repeated as
 // a plain cluster launch if the launch check refused it.
-static ttns_status kinetic_envs(ttns_tree* t) {
-  KernelParams P2 = t->P;
-  P2.dt = 0.0;
-  P2.n_steps = 1;
-  CUDA_TRY(launch_sweep(P2, 2, t->grid, t->cluster, !(t->opt.launch_flags & 1), t->stream));
+// One launch of a single-pass phase of the persistent kernel (2: the kinetic operator's
+// environment pass, 3: the completion of grown bonds, 0: the environment pass), with the
+// repeat of a refused launch as a plain cluster launch (nothing ran in the refused one).
+static ttns_status run_phase(ttns_tree* t, int phase, const char* what) {
+  KernelParams Pp = t->P;
+  Pp.dt = 0.0;
+  Pp.n_steps = 1;
+  CUDA_TRY(launch_sweep(Pp, phase, t->grid, t->cluster, !(t->opt.launch_flags & 1), t->stream));
   CUDA_TRY(cudaStreamSynchronize(t->stream));
   Ctl h;
   CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
@@ -781,13 +786,15 @@ static ttns_status kinetic_envs(ttns_tree* t) {
     ++t->launch_fallbacks;
     h.status = h.err_where = h.err_node = 0;
     CUDA_TRY(cudaMemcpy(t->ctl, &h, sizeof(Ctl), cudaMemcpyHostToDevice));
-    CUDA_TRY(launch_sweep(P2, 2, t->grid, t->cluster, 0, t->stream));
+    CUDA_TRY(launch_sweep(Pp, phase, t->grid, t->cluster, 0, t->stream));
     CUDA_TRY(cudaStreamSynchronize(t->stream));
     CUDA_TRY(cudaMemcpy(&h, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
   }
-  if (h.status != 0) return fail((ttns_status)h.status, std::string("kinetic environment pass: ") + status_text(h));
+  if (h.status != 0) return fail((ttns_status)h.status, std::string(what) + status_text(h));
   return TTNS_OK;
 }
+
+static ttns_status kinetic_envs(ttns_tree* t) { return run_phase(t, 2, "kinetic environment pass: "); }
 
 extern "C" ttns_status ttns_energy_surfaces(ttns_tree* t, int tree_idx, double sigma_tol, double* tes, double* pes,
                                             double* sigma, int* n_bath) {
@@ -872,9 +879,10 @@ extern "C" ttns_status ttns_energy_surfaces(ttns_tree* t, int tree_idx, double s
   return TTNS_OK;
 }
 
-extern "C" ttns_status ttns_bond_entropies(ttns_tree* t, int tree_idx, double* S_out) {
-  if (!t || !S_out) return fail(TTNS_E_INVALID, "NULL argument");
-  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+// Spectra of rho_S (node 0) and of every non-root node's parent-bond density matrix: the
+// downward pass of bond densities and the batched Hermitian Jacobi; ev holds 64 values per
+// node (the first ns[v] are the eigenvalues of node v's matrix).
+static ttns_status bond_spectra(ttns_tree* t, int tree_idx, std::vector<double>* ev, std::vector<int>* ns_out) {
   ttns_status s = ttns_sync(t);
   if (s != TTNS_OK) return s;
   const TreeDesc& td = t->C.trees[tree_idx];
@@ -889,7 +897,8 @@ extern "C" ttns_status ttns_bond_entropies(ttns_tree* t, int tree_idx, double* S
   if ((s = surface_scratch(t, std::max<long long>(total, 1))) != TTNS_OK) return s;
   // rho_S and the bond densities live in one buffer (obs): offsets relative to obs as double2
   std::vector<long long> offs(n);
-  std::vector<int> ns(n);
+  std::vector<int>& ns = *ns_out;
+  ns.assign(n, 0);
   offs[0] = (t->o_rho) / 2;
   ns[0] = td.n_el;
   for (int v = 1; v < n; ++v) {
@@ -900,10 +909,20 @@ extern "C" ttns_status ttns_bond_entropies(ttns_tree* t, int tree_idx, double* S
   if ((s = eig_batch(t, (const double2*)t->obs, offs, ns, sc + o_ev, nullptr, (long long*)(sc + o_offs),
                      (int*)(sc + o_ns))) != TTNS_OK)
     return s;
-  std::vector<double> ev(64LL * n);
-  CUDA_TRY(cudaMemcpyAsync(ev.data(), sc + o_ev, sizeof(double) * 64 * n, cudaMemcpyDeviceToHost, t->stream));
+  ev->assign(64LL * n, 0.0);
+  CUDA_TRY(cudaMemcpyAsync(ev->data(), sc + o_ev, sizeof(double) * 64 * n, cudaMemcpyDeviceToHost, t->stream));
   CUDA_TRY(cudaStreamSynchronize(t->stream));
-  for (int v = 0; v < n; ++v) {
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_bond_entropies(ttns_tree* t, int tree_idx, double* S_out) {
+  if (!t || !S_out) return fail(TTNS_E_INVALID, "NULL argument");
+  if (tree_idx < 0 || tree_idx >= (int)t->C.trees.size()) return fail(TTNS_E_INVALID, "tree_idx out of range");
+  std::vector<double> ev;
+  std::vector<int> ns;
+  ttns_status s = bond_spectra(t, tree_idx, &ev, &ns);
+  if (s != TTNS_OK) return s;
+  for (int v = 0; v < (int)ns.size(); ++v) {
     double S = 0.0;
     for (int a = 0; a < ns[v]; ++a) {
       const double l = ev[(long long)v * 64 + a];
@@ -912,6 +931,145 @@ extern "C" ttns_status ttns_bond_entropies(ttns_tree* t, int tree_idx, double* S
     S_out[v] = S;
   }
   return TTNS_OK;
+}
+
+// Adaptive bond dimension: the tree is rebuilt with the larger bonds, every tensor copied
+// with zero slices on the grown legs, and the completion program (children first: the QR of
+// each grown child toward its parent, whose zero columns get the identity reflector, and the
+// absorb of R into the parent) runs before a fresh environment pass; the new tree set takes
+// the place of the old one in the same handle.
+extern "C" ttns_status ttns_grow_bonds(ttns_tree* t, const int* new_bond, int n_nodes, int* n_grown) {
+  if (!t || !new_bond) return fail(TTNS_E_INVALID, "NULL argument");
+  if (n_grown) *n_grown = 0;
+  if (t->C.trees.size() != 1) return fail(TTNS_E_INVALID, "bond growth works on a single-tree set");
+  const HostTree h = t->C.host[0];
+  if (n_nodes != h.n()) return fail(TTNS_E_INVALID, "n_nodes does not match the tree");
+  ttns_status s = ttns_sync(t);
+  if (s != TTNS_OK) return s;
+  TreeInput in = t->inputs[0];
+  in.bond_req.assign(h.n(), 0);
+  for (int v = 1; v < h.n(); ++v) in.bond_req[v] = std::max(h.bond[v], new_bond[v]);
+  ttns_tree* t2 = new ttns_tree();
+  std::vector<TreeInput> ins{in};
+  if ((s = compile_inputs(std::move(ins), t->opt, t2)) != TTNS_OK) {
+    delete t2;
+    return s;
+  }
+  const HostTree& h2 = t2->C.host[0];
+  std::vector<int> grown;
+  for (int v = 1; v < h2.n(); ++v)
+    if (h2.bond[v] > h.bond[v]) grown.push_back(v);
+  if (grown.empty()) {
+    delete t2;
+    return TTNS_OK;
+  }
+  // the completion program, children first
+  {
+    Compiled& C2 = t2->C;
+    TreeDesc& td2 = C2.trees[0];
+    const long long gthr = t->opt.grid_threshold > 0 ? t->opt.grid_threshold : 16384;
+    const long long qthr = t->opt.qr_grid_threshold > 0 ? t->opt.qr_grid_threshold : 65536;
+    td2.grow_first = (int)C2.prog.size();
+    for (auto it = grown.rbegin(); it != grown.rend(); ++it) {
+      const int v = *it, p = h2.parent[v];
+      Instr Q{};
+      Q.op = OP_QR;
+      Q.tree = 0;
+      Q.node = td2.node0 + v;
+      Q.leg = h2.leg_of(v, p);
+      Q.D = C2.nodes[Q.node].dims[Q.leg];
+      Q.team = C2.nodes[Q.node].size >= qthr ? TEAM_GRID : TEAM_CLUSTER;
+      C2.prog.push_back(Q);
+      Instr A{};
+      A.op = OP_ABSORB;
+      A.tree = 0;
+      A.node = td2.node0 + p;
+      A.leg = h2.leg_of(p, v);
+      A.D = C2.nodes[A.node].dims[A.leg];
+      A.team = C2.nodes[A.node].size >= gthr ? TEAM_GRID : TEAM_CLUSTER;
+      C2.prog.push_back(A);
+    }
+    td2.grow_count = (int)C2.prog.size() - td2.grow_first;
+  }
+  if ((s = device_init(t2)) != TTNS_OK) {
+    std::string keep = g_err;
+    ttns_free(t2);
+    g_err = keep;
+    return s;
+  }
+  auto abort_with = [&](ttns_status st) {
+    std::string keep = g_err;
+    ttns_free(t2);
+    g_err = keep;
+    return st;
+  };
+  // the state, the trajectory record, the Krylov history and the counters
+  const TreeDesc& td = t->C.trees[0];
+  const TreeDesc& td2 = t2->C.trees[0];
+  for (int v = 0; v < h.n(); ++v) {
+    const NodeDesc& so = t->C.nodes[td.node0 + v];
+    const NodeDesc& dn = t2->C.nodes[td2.node0 + v];
+    bool shapes = so.nl == dn.nl && so.off + so.size <= t->C.pool_size && dn.off + dn.size <= t2->C.pool_size;
+    for (int l = 0; shapes && l < so.nl; ++l) shapes = so.dims[l] <= dn.dims[l];
+    if (!shapes) return abort_with(fail(TTNS_E_INVALID, "grown tree does not contain the old tensor shapes"));
+    cudaError_t e = launch_pad_copy(t->pool, so, t2->pool, dn, t2->stream);
+    if (e != cudaSuccess) return abort_with(fail(TTNS_E_CUDA, std::string("pad copy: ") + cudaGetErrorString(e)));
+  }
+  // the trajectory record exists only when recording is on (traj_off < 0 otherwise); both
+  // trees have the same recording settings and electronic dimension
+  if (td.traj_off >= 0 && td2.traj_off >= 0 && t->P.max_record == t2->P.max_record && td.n_el == td2.n_el) {
+    const size_t traj = (size_t)t->P.max_record * td.n_el * td.n_el;
+    if (td.traj_off + (long long)traj > t->C.pool_size || td2.traj_off + (long long)traj > t2->C.pool_size)
+      return abort_with(fail(TTNS_E_INVALID, "trajectory region outside the pool"));
+    if (cudaMemcpyAsync(t2->pool + td2.traj_off, t->pool + td.traj_off, traj * sizeof(double2),
+                        cudaMemcpyDeviceToDevice, t2->stream) != cudaSuccess ||
+        cudaMemcpyAsync(t2->traj_count, t->traj_count, sizeof(int), cudaMemcpyDeviceToDevice, t2->stream) != cudaSuccess)
+      return abort_with(fail(TTNS_E_CUDA, "trajectory copy failed"));
+  }
+  if (t2->C.n_hist == t->C.n_hist &&
+      cudaMemcpyAsync(t2->mhist, t->mhist, sizeof(int) * std::max(t->C.n_hist, 1), cudaMemcpyDeviceToDevice,
+                      t2->stream) != cudaSuccess)
+    return abort_with(fail(TTNS_E_CUDA, "history copy failed"));
+  Ctl hc;
+  if (cudaMemcpy(&hc, t->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return abort_with(fail(TTNS_E_CUDA, "control block read failed"));
+  hc.bar_count = 0;
+  hc.bar_gen = 0;
+  hc.status = hc.err_where = hc.err_node = 0;
+  if (cudaMemcpy(t2->ctl, &hc, sizeof(Ctl), cudaMemcpyHostToDevice) != cudaSuccess)
+    return abort_with(fail(TTNS_E_CUDA, "control block write failed"));
+  if ((s = run_phase(t2, 3, "completion of grown bonds: ")) != TTNS_OK) return abort_with(s);
+  if ((s = run_phase(t2, 0, "environment pass after growth: ")) != TTNS_OK) return abort_with(s);
+  t2->t_fs = t->t_fs;
+  t2->launch_fallbacks += t->launch_fallbacks;
+  std::swap(*t, *t2);
+  ttns_free(t2);  // the old tree set
+  if (n_grown) *n_grown = (int)grown.size();
+  return TTNS_OK;
+}
+
+extern "C" ttns_status ttns_adapt_bonds(ttns_tree* t, double eps, int step, int d_max, int* n_grown) {
+  if (!t) return fail(TTNS_E_INVALID, "NULL argument");
+  if (n_grown) *n_grown = 0;
+  if (!(eps >= 0.0) || step < 1 || d_max < 1) return fail(TTNS_E_INVALID, "eps >= 0, step >= 1 and d_max >= 1 required");
+  if (t->C.trees.size() != 1) return fail(TTNS_E_INVALID, "bond growth works on a single-tree set");
+  std::vector<double> ev;
+  std::vector<int> ns;
+  ttns_status s = bond_spectra(t, 0, &ev, &ns);
+  if (s != TTNS_OK) return s;
+  const HostTree& h = t->C.host[0];
+  std::vector<int> req(h.n(), 0);
+  bool any = false;
+  for (int v = 1; v < h.n(); ++v) {
+    double lo = 1e300;
+    for (int a = 0; a < ns[v]; ++a) lo = std::min(lo, ev[(long long)v * 64 + a]);
+    if (h.bond[v] < d_max && lo > eps) {
+      req[v] = std::min(h.bond[v] + step, d_max);
+      any = true;
+    }
+  }
+  if (!any) return TTNS_OK;
+  return ttns_grow_bonds(t, req.data(), h.n(), n_grown);
 }
 
 extern "C" ttns_status ttns_observables(ttns_tree* t, int tree_idx, double* norm, double* energy) {
@@ -1029,12 +1187,13 @@ extern "C" ttns_status ttns_get_node(ttns_tree* t, int tree_idx, int node, doubl
 }
 
 // Checkpoint format (little-endian host types):
-//   "TTNSCKP2", int64 n_trees, every tree's problem (TreeInput: n_el, shifted-free H_S,
-//   patterns, chains, dims, requested bonds, ER layout, initial amplitudes), int32 record and
+//   "TTNSCKP3", int64 n_trees, every tree's problem (TreeInput: n_el, shifted-free H_S,
+//   patterns, chains, dims, requested bonds, ER layout, initial amplitudes, the per-node bond
+//   requests of a grown tree), int32 record and
 //   max_record, then int64 {pool size, history slots, trees, 0}, double t_fs, the complex pool
 //   (tensors, environment blocks, trajectory), the Krylov-length history, the trajectory
 //   counters and the device control block.
-static const char kMagic[8] = {'T', 'T', 'N', 'S', 'C', 'K', 'P', '2'};
+static const char kMagic[8] = {'T', 'T', 'N', 'S', 'C', 'K', 'P', '3'};
 
 namespace {
 struct Writer {
@@ -1078,6 +1237,7 @@ void write_input(Writer& w, const TreeInput& in) {
   w.put(in.er_tree);
   w.put(in.D_er);
   w.put_vec(in.psi_el);
+  w.put_vec(in.bond_req);
 }
 
 bool read_input(Reader& r, TreeInput& in) {
@@ -1105,6 +1265,7 @@ bool read_input(Reader& r, TreeInput& in) {
   r.get(in.er_tree);
   r.get(in.D_er);
   r.get_vec(in.psi_el, kMaxVec);
+  r.get_vec(in.bond_req, kMaxVec);
   if (!r.ok) return false;
   // the shapes must agree with each other (the values were validated when the file was written)
   const size_t ne = (size_t)in.n_env;

@@ -104,6 +104,8 @@ struct TreeDesc {
   int obs_count;
   int heff_terms;     // term list of H_eff(root) and of T_eff(root)
   int teff_terms;
+  int grow_first;     // completion of grown bonds (QR of each grown child, absorb into its parent)
+  int grow_count;
 };
 
 // Device-side control block (status word, barrier, counters).

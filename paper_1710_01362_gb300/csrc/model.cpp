@@ -188,6 +188,13 @@ HostTree build_host_tree(const TreeInput& in) {
     }
     t.chain_nodes.push_back(nodes);
   }
+  if (!in.bond_req.empty()) {
+    if ((int)in.bond_req.size() != t.n()) throw std::invalid_argument("bond requests do not match the tree's nodes");
+    for (int v = 1; v < t.n(); ++v) {
+      if (in.bond_req[v] < 1) throw std::invalid_argument("bond request below 1");
+      req[v] = in.bond_req[v];
+    }
+  }
   // requested bond dimensions (any size: a request beyond the Hilbert space asks for the full
   // bond) are clamped first; what remains must fit the device code's leg limit
   clamp_bonds(t, req);

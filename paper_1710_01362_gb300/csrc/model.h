@@ -52,6 +52,10 @@ struct TreeInput {
   int er_tree = 0;
   int D_er = 0;
   std::vector<cplx> psi_el;
+  // requested parent-bond dimension of every node (node order of the built tree; the root's
+  // entry unused), replacing the per-chain and ER requests when not empty: a tree whose bonds
+  // were grown during the run
+  std::vector<int> bond_req;
 };
 
 HostTree build_host_tree(const TreeInput& in);

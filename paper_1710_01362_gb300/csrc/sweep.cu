@@ -1404,6 +1404,57 @@ __device__ __noinline__ bool tc_task(const KernelParams& P, const NodeDesc& nd, 
   const int my_row = q4 * 32 + lane;
   const int c_lo = half * (Npad / 2), c_hi = c_lo + Npad / 2;
   for (int c = c_lo; c < c_hi; ++c) sums[my_row * ldsum + c] = 0.0f;
+  // Sparse factors with one entry per row (a, a^+, a diagonal): their tables go to shared
+  // memory after the operand planes, so that every z of a batch is one independent load of x
+  // (else each z would chain a table load and an x load).  Other groups keep tc_z.
+  struct SpHdr {
+    int sp, leg, st, D;
+    float inv_st, inv_D;
+    int off, pad;
+  };
+  unsigned char* tail = B + S::parts * b_plane;
+  SpHdr* hdr = reinterpret_cast<SpHdr*>(tail);
+  const long long tail_off = (long long)(tail - dyn_smem);
+  bool fast = nterm <= TTNS_MAX_TERMS;
+  int ntab = 0;
+  for (int tl = 0; tl < nterm && fast; ++tl) {
+    const int q = tp.gfirst[g] + tl;
+    const Term& T_ = os.terms[tp.gterm[q]];
+    if (T_.nf == 2) {
+      const Factor& f = T_.f[1 - tp.gdense[q]];
+      if (f.nnz != 1) fast = false;
+      ntab += nd.dims[f.leg];
+    }
+  }
+  const long long hdr_bytes = ((long long)nterm * sizeof(SpHdr) + 15) & ~15LL;
+  float2* tvals = reinterpret_cast<float2*>(tail + hdr_bytes);
+  int* tcols = reinterpret_cast<int*>(tvals + ntab);
+  fast = fast && tail_off + hdr_bytes + (long long)ntab * 12 <= P.smem_bytes;
+  if (fast) {
+    int off = 0;
+    for (int tl = 0; tl < nterm; ++tl) {  // every thread walks the same terms
+      const int q = tp.gfirst[g] + tl;
+      const Term& T_ = os.terms[tp.gterm[q]];
+      SpHdr h{};
+      if (T_.nf == 2) {
+        const Factor& f = T_.f[1 - tp.gdense[q]];
+        h.sp = 1;
+        h.leg = f.leg;
+        h.st = nd.strides[f.leg];
+        h.D = nd.dims[f.leg];
+        h.inv_st = nd.inv_strides[f.leg];
+        h.inv_D = nd.inv_dims[f.leg];
+        h.off = off;
+        for (int i = tid; i < h.D; i += NT) {
+          tvals[off + i] = P.pool32[f.sp + i];
+          tcols[off + i] = (int)P.pool32[f.sp + h.D + i].x;
+        }
+        off += h.D;
+      }
+      if (tid == 0) hdr[tl] = h;
+    }
+    __syncthreads();
+  }
   bool ok = true;
   const int kbeg = part * tp.gkpart[g];
   const int kend = min(ktot, kbeg + tp.gkpart[g]);
@@ -1411,7 +1462,74 @@ __device__ __noinline__ bool tc_task(const KernelParams& P, const NodeDesc& nd, 
     const int nk = min(chunk_kc, kend - kc0);   // a multiple of KSC
     const int Kr = 2 * nk;
     // A: rows of the tile x (term, k) of the chunk
-    {
+    if (fast) {
+      const int per_row = nk / G;
+      const int nitems = kTcRows * per_row;
+      for (int it0 = tid; it0 < nitems; it0 += 4 * NT) {
+        long long xi[4][G];
+        V cv[4][G];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int item = it0 + u * NT;
+          const int row = item % kTcRows, kq = item / kTcRows;
+          const int R = r0 + row;
+          const bool in = item < nitems && R < rows;
+          long long base = 0;
+          if (in) {
+            const int outer = fdivu(R, st, tp.inv_st[g]);
+            base = (long long)outer * D * st + (R - outer * st);
+          }
+#pragma unroll
+          for (int j = 0; j < G; ++j) {
+            const int kg = kc0 + kq * G + j;
+            xi[u][j] = -1;
+            cv[u][j].x = (T)1;
+            cv[u][j].y = (T)0;
+            if (in && kg < nterm * D) {
+              const int tl = kg / D, kk = kg - tl * D;
+              const int el = (int)(base + (long long)kk * st);
+              const SpHdr h = hdr[tl];
+              if (h.sp) {
+                const int qq = fdivu(el, h.st, h.inv_st);
+                const int i = qq - fdivu(qq, h.D, h.inv_D) * h.D;
+                xi[u][j] = (long long)(el - i * h.st) + (long long)tcols[h.off + i] * h.st;
+                const float2 v = tvals[h.off + i];
+                cv[u][j].x = (T)v.x;
+                cv[u][j].y = (T)v.y;
+              } else {
+                xi[u][j] = el;
+              }
+            }
+          }
+        }
+        V xv[4][G];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int j = 0; j < G; ++j) {
+            if (xi[u][j] >= 0) {
+              xv[u][j] = cvt<T>(x[xi[u][j]]);
+            } else {
+              xv[u][j].x = (T)0;
+              xv[u][j].y = (T)0;
+            }
+          }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int item = it0 + u * NT;
+          if (item >= nitems) break;
+          const int row = item % kTcRows, kq = item / kTcRows;
+#pragma unroll
+          for (int j = 0; j < G; ++j) {
+            V z;
+            z.x = z.y = (T)0;
+            cmac<T>(z, cv[u][j], xv[u][j]);
+            tc::put_split_f<KIND>(A, a_plane, row, 2 * (kq * G + j), Kr, (float)z.x);
+            tc::put_split_f<KIND>(A, a_plane, row, 2 * (kq * G + j) + 1, Kr, (float)z.y);
+          }
+        }
+      }
+    } else {
       const int per_row = nk / G;
       const int nitems = kTcRows * per_row;
       for (int it0 = tid; it0 < nitems; it0 += 4 * NT) {
@@ -2506,8 +2624,8 @@ __device__ void run(const KernelParams& P, int phase) {
   if (P.batched) {
     for (int tree = cluster_id; tree < P.n_trees; tree += n_clusters) {
       const TreeDesc& td = P.trees[tree];
-      const int first = phase == 0 ? td.init_first : (phase == 2 ? td.obs_first : td.prog_first);
-      const int count = phase == 0 ? td.init_count : (phase == 2 ? td.obs_count : td.prog_count);
+      const int first = phase == 0 ? td.init_first : (phase == 2 ? td.obs_first : (phase == 3 ? td.grow_first : td.prog_first));
+      const int count = phase == 0 ? td.init_count : (phase == 2 ? td.obs_count : (phase == 3 ? td.grow_count : td.prog_count));
       const int nst = phase == 1 ? P.n_steps : 1;
       for (int s = 0; s < nst; ++s) {
         for (int k = 0; k < count; ++k) {
@@ -2528,8 +2646,8 @@ __device__ void run(const KernelParams& P, int phase) {
   gt.spin_limit = P.spin_limit;
   gt.csize = cs;
   const TreeDesc& td = P.trees[0];
-  const int first = phase == 0 ? td.init_first : (phase == 2 ? td.obs_first : td.prog_first);
-  const int count = phase == 0 ? td.init_count : (phase == 2 ? td.obs_count : td.prog_count);
+  const int first = phase == 0 ? td.init_first : (phase == 2 ? td.obs_first : (phase == 3 ? td.grow_first : td.prog_first));
+  const int count = phase == 0 ? td.init_count : (phase == 2 ? td.obs_count : (phase == 3 ? td.grow_count : td.prog_count));
   const int nst = phase == 1 ? P.n_steps : 1;
   int prev = TEAM_GRID;
   for (int s = 0; s < nst; ++s) {
@@ -2771,6 +2889,31 @@ __global__ void k_wait_selftest(Ctl* ctl, long long spin_limit, int skip) {
 cudaError_t launch_wait_selftest(Ctl* ctl, long long spin_limit, int skip, cudaStream_t st) {
   void* args[] = {&ctl, &spin_limit, &skip};
   return cudaLaunchCooperativeKernel((void*)k_wait_selftest, dim3(2), dim3(NT), args, 0, st);
+}
+
+// Copy of a node tensor into a tensor of the same legs with larger (or equal) dimensions,
+// zero on the new indices (row-major, legs in the node's order)
+__global__ void k_pad_copy(const double2* src, NodeDesc so, double2* dst, NodeDesc dn) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < dn.size;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long rem = idx, off = 0;
+    bool in = true;
+    for (int l = 0; l < dn.nl; ++l) {
+      const long long i = rem / dn.strides[l];
+      rem -= i * dn.strides[l];
+      in = in && i < so.dims[l];
+      off += i * so.strides[l];
+    }
+    dst[idx] = in ? src[off] : make_double2(0.0, 0.0);
+  }
+}
+
+cudaError_t launch_pad_copy(const double2* src_pool, const NodeDesc& so, double2* dst_pool, const NodeDesc& dn,
+                            cudaStream_t st) {
+  long long nb = (dn.size + 255) / 256;
+  nb = nb > 4096 ? 4096 : (nb < 1 ? 1 : nb);
+  k_pad_copy<<<(int)nb, 256, 0, st>>>(src_pool + so.off, so, dst_pool + dn.off, dn);
+  return cudaGetLastError();
 }
 
 // FP32 mirror of the pool (after the pool was written from the host)

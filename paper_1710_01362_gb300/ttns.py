@@ -30,7 +30,7 @@ EXPORTS = [
     "ttns_chain_ohmic", "ttns_chain_from_modes", "ttns_plan", "ttns_selftest_wait_timeout",
     "ttns_rho_from_root_noalloc", "ttns_autotune", "ttns_selftest_tc_gemm", "ttns_mlp_gemm", "ttns_mlp_colsum",
     "ttns_mlp_diff", "ttns_mlp_adam", "ttns_mlp_status", "ttns_energy_surfaces", "ttns_bond_entropies",
-    "ttns_cluster_modes",
+    "ttns_cluster_modes", "ttns_grow_bonds", "ttns_adapt_bonds",
 ]
 
 
@@ -100,6 +100,8 @@ def lib():
         L.ttns_trajectory.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, C.POINTER(C.c_int)]
         L.ttns_energy_surfaces.argtypes = [C.c_void_p, C.c_int, C.c_double, dp, dp, dp, C.POINTER(C.c_int)]
         L.ttns_bond_entropies.argtypes = [C.c_void_p, C.c_int, dp]
+        L.ttns_grow_bonds.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]
+        L.ttns_adapt_bonds.argtypes = [C.c_void_p, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_int)]
         ip = C.POINTER(C.c_int)
         L.ttns_cluster_modes.argtypes = [C.c_int, C.c_int, dp, C.c_int, ip, C.c_int, ip, dp, dp, ip]
         L.ttns_populations_device.argtypes = [C.c_void_p, C.c_void_p]
@@ -384,6 +386,31 @@ class Tree:
         out = np.zeros(self.n_nodes(k))
         _check(lib().ttns_bond_entropies(self.h, k, _dptr(out)))
         return out
+
+    def bonds(self, k: int = 0) -> list:
+        """Parent-bond dimension of every node (the root's entry 0)."""
+        out = [0]
+        for v in range(1, self.n_nodes(k)):
+            nl = C.c_int()
+            dims = (C.c_int * 8)()
+            _check(lib().ttns_node_info(self.h, k, v, C.byref(nl), dims, None))
+            out.append(dims[0])
+        return out
+
+    def grow_bonds(self, new_bond) -> int:
+        """Raises parent-bond dimensions (new_bond[v] for node v; see ttns_grow_bonds); returns
+        the number of grown bonds."""
+        n = self.n_nodes(0)
+        req = (C.c_int * n)(*[int(x) for x in new_bond])
+        g = C.c_int()
+        _check(lib().ttns_grow_bonds(self.h, req, n, C.byref(g)))
+        return g.value
+
+    def adapt_bonds(self, eps: float, step: int, d_max: int) -> int:
+        """The adaptive rule (ttns_adapt_bonds); returns the number of grown bonds."""
+        g = C.c_int()
+        _check(lib().ttns_adapt_bonds(self.h, eps, step, d_max, C.byref(g)))
+        return g.value
 
     def populations_device(self, dev_ptr: int) -> None:
         _check(lib().ttns_populations_device(self.h, C.c_void_p(dev_ptr)))
