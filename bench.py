@@ -59,9 +59,9 @@ WORKLOADS = {
                               dt_fs=0.5)),
 }
 PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "fp32": 3}
-DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (contractions) + f64 (Lanczos, QR, gauge)",
-         "bf16x3": "bf16x3 (contractions) + f64 (Lanczos, QR, gauge)",
-         "fp32": "f32 (contractions) + f64 (Lanczos, QR, gauge)"}
+DTYPE = {"fp64": "f64", "tf32x3": "tf32x3 (contractions) + f64 (Lanczos) + double-single (QR, gauge)",
+         "bf16x3": "bf16x3 (contractions) + f64 (Lanczos) + double-single (QR, gauge)",
+         "fp32": "f32 (contractions) + f64 (Lanczos) + double-single (QR, gauge)"}
 
 
 def make_problems(name: str):
