@@ -2,12 +2,13 @@
 // compiled one-site TDVP step (Results, "TTNS for vibronic quantum dynamics":
 // every tensor evolved in turn with its local effective Hamiltonian) for n steps.
 //
-// Execution model (GB300: 152 SMs, FP64 at 1/64 of the FP32 rate with a long
-// dependent latency, hardware cluster barriers ~0.2 us, software grid barriers
-// ~2.3 us):
-//   * a "team" executes one instruction: either one thread-block cluster
-//     (hardware barrier; used for every node of small trees and for chain sites)
-//     or the whole grid (software barrier; used for the large electronic root);
+// Execution model (GB300: 152 SMs, FP64 at about 1/80 of the FP32 rate with a long
+// dependent latency, and the FP64 <-> FP32 conversions on the same narrow pipe; hardware
+// cluster barriers ~0.2 us; the software grid barrier meets at the cluster barrier first):
+//   * a "team" executes one instruction: either one thread-block cluster (hardware
+//     barrier; small tensors, and every QR below the QR threshold) or the whole grid
+//     (software barrier; Krylov exponentials, environment updates and absorbs of tensors
+//     above the grid threshold);
 //   * in batched mode every cluster advances its own trees independently;
 //   * reductions are deterministic: per-CTA partials, then a fixed-order sum
 //     that every CTA computes identically (no floating-point atomics);
@@ -337,9 +338,9 @@ __device__ __forceinline__ typename C2<T>::t mode_dot(const MT* row, int D, cons
 
 // Staging of one op's operands in shared memory.  Every node's operators (the
 // environment blocks flowing into it and its constant operators) are contiguous in the
-// pool, so an op stages one or two regions with asynchronous 16-byte copies (cp.async),
-// plus its term list; a factor's shared-memory slot is its offset inside the staged
-// regions.  Matrices stay FP64 (double2) in shared memory and are converted on use.
+// pool, so an op stages one or two regions with asynchronous copies (cp.async), plus its
+// term list; a factor's shared-memory slot is its offset inside the staged regions.  The
+// matrices are staged in the compute type: FP64 from the pool, or FP32 from its mirror.
 extern __shared__ __align__(16) unsigned char dyn_smem[];
 
 // operator data in the compute type: the FP64 pool, or its FP32 mirror
