@@ -105,3 +105,17 @@ def test_adaptive_rule_grows_the_bonds_with_large_smallest_weights():
     assert np.abs(st.to_dense() - ref.to_dense()).max() < 1e-13
     # nothing exceeds eps = 1 (weights are at most 1 and the smallest below 1 / D)
     assert st.adapt_bonds(1.0, 2, 6) == []
+
+
+def test_growth_of_an_er_tree_to_full_dimension_is_exact():
+    # ER nodes carry no physical leg: their bonds are clamped by products of child bonds only
+    p = W.sf_small(seed=5, n_env=2, L=2, d=3, D=1, n_modes=4, dt=0.5, er_tree=True, D_er=1)
+    st, ex = TTNS(p), Exact(p)
+    assert st.tree.kind[1] == "er"
+    st.grow_bonds([0] + [1 << 20] * (st.tree.n - 1))
+    full = TTNS(W.sf_small(seed=5, n_env=2, L=2, d=3, D=64, n_modes=4, dt=0.5, er_tree=True, D_er=64))
+    assert st.tree.bond == full.tree.bond
+    for _ in range(10):
+        st.step(p.dt)
+    psi = ex.state(st.t)
+    assert np.abs(st.to_dense() - psi).max() < 5e-8
