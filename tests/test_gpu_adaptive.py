@@ -120,3 +120,16 @@ def test_growth_rejects_batches_and_bad_sizes():
     with pytest.raises(ttns.TTNSError):
         g.adapt_bonds(-1.0, 2, 6)
     g.close()
+
+
+def test_er_tree_growth_to_full_dimension_at_t0_is_exact():
+    # ER tensors have three bond legs and no physical leg
+    p = W.sf_small(seed=5, n_env=2, L=2, d=3, D=1, n_modes=4, dt=0.5, er_tree=True, D_er=1)
+    ex = Exact(p)
+    g = ttns.Tree(p, precision=ttns.TTNS_FP64)
+    g.grow_bonds([0] + [1 << 20] * (g.n_nodes() - 1))
+    full = TTNS(W.sf_small(seed=5, n_env=2, L=2, d=3, D=64, n_modes=4, dt=0.5, er_tree=True, D_er=64))
+    assert g.bonds() == full.tree.bond
+    g.step(p.dt, 10)
+    np.testing.assert_allclose(g.rho(), ex.rho_el(ex.state(10 * p.dt)), atol=1e-8)
+    g.close()
